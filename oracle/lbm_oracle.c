@@ -1,0 +1,358 @@
+/*
+ * lbm_oracle.c -- FP64 CPU oracle for one time step of the urban-wind LBM-LES solver.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct definition that the
+ * CUDA path is checked against.  Only the test suite, the smoke check and the CPU-baseline leg of
+ * the benchmark may load it; the product library never links, calls or falls back to it.  It
+ * shares no code, header, table or constant with the CUDA sources.
+ *
+ * What it computes (paper App. D, equations numbered in order of appearance D.1 ... D.11):
+ *   - D3Q19 lattice, c_s^2 = 1/3, weights fixed by 2nd/4th-order isotropy (App. D, text before D.1)
+ *   - moments rho = sum f_i, rho u = sum c_i f_i                                   (D.1)
+ *   - second-order Hermite equilibrium f_i^eq(rho, u)                              (D.4)
+ *   - non-equilibrium flux Pi^(1) = sum c c (f - f^eq), Q = sqrt(2 Pi:Pi)          (D.8, D.10)
+ *   - tau_eff = 1/2 [tau + sqrt(tau^2 + 2 (C Delta)^2 Q / (rho c_s^4))], Delta = 1  (D.11)
+ *   - SRT-BGK collision f* = f - (f - f^eq)/tau_eff                                (D.2)
+ *   - streaming f_i(x + c_i, t + 1) = f*_i(x, t)                                   (D.3)
+ *   - halfway (mid-grid) bounce-back at solid cells and no-slip faces  (App. D, last paragraph)
+ *   - equilibrium velocity boundary cells (Sec. 3, boundary-condition paragraph)
+ *   - optional uniform body force by Guo's forcing (App. E names the method; used here only for
+ *     the laminar channel check)
+ *
+ * The step is written as a two-lattice PULL: Fout(x) is computed from Fin (the post-collision
+ * state of the previous step) by gathering each population from its upstream neighbour and then
+ * colliding.  Observed state = post-collision populations F*.
+ *
+ * Readings where the paper is silent (each one is listed in the design notes of the repository):
+ *   - lattice units, Delta t = Delta x = Delta = 1, so nu_0 = (tau - 1/2)/3;
+ *   - Pi^(1) is taken from the pre-collision (post-stream) populations against f^eq of the same
+ *     populations; Q sums all nine tensor components;
+ *   - equilibrium boundary cells hold f^eq(rho_b, u_b(z)) and never gather;
+ *   - outflow faces are zero-gradient: a population entering from outside the face is the
+ *     same-direction population leaving the adjacent in-domain cell one step earlier;
+ *   - free-slip faces reflect specularly (the normal velocity component is mirrored);
+ *   - periodic faces wrap;
+ *   - edges and corners: a source position outside the domain is resolved axis by axis
+ *     (wrap / clamp / clamp + mirror); if any out-of-range axis is a no-slip face, or if the
+ *     resolved source cell is solid, the population is bounced back from the cell itself.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORQ 19
+
+/* face kinds, oracle-private numbering */
+enum { OR_PERIODIC = 0, OR_INFLOW = 1, OR_OUTFLOW = 2, OR_FREESLIP = 3, OR_NOSLIP = 4 };
+/* cell kinds */
+enum { OR_FLUID = 0, OR_SOLID = 1, OR_EQ = 2 };
+
+static int oc[ORQ][3];     /* lattice velocities */
+static double ow[ORQ];     /* weights */
+static int oopp[ORQ];      /* opposite direction */
+static int omir[3][ORQ];   /* direction with component a negated */
+static int otab_ready = 0;
+
+/* D3Q19 = every c in {-1,0,1}^3 with |c|^2 <= 2; weight from |c|^2 alone (1/3, 1/18, 1/36).
+ * These are the only weights that give sum w = 1, sum w c_a c_b = delta/3 and the 4th-order
+ * isotropic tensor c_s^4 (dd + dd + dd) on this velocity set; the tests check exactly that. */
+static void tables(void)
+{
+    if (otab_ready) return;
+    int n = 0;
+    for (int c2 = 0; c2 <= 2; ++c2)
+        for (int z = -1; z <= 1; ++z)
+            for (int y = -1; y <= 1; ++y)
+                for (int x = -1; x <= 1; ++x)
+                    if (x * x + y * y + z * z == c2) {
+                        oc[n][0] = x; oc[n][1] = y; oc[n][2] = z;
+                        ow[n] = (c2 == 0) ? 1.0 / 3.0 : (c2 == 1) ? 1.0 / 18.0 : 1.0 / 36.0;
+                        ++n;
+                    }
+    for (int i = 0; i < ORQ; ++i)
+        for (int j = 0; j < ORQ; ++j) {
+            if (oc[j][0] == -oc[i][0] && oc[j][1] == -oc[i][1] && oc[j][2] == -oc[i][2]) oopp[i] = j;
+            for (int a = 0; a < 3; ++a) {
+                int ok = 1;
+                for (int b = 0; b < 3; ++b) ok &= (oc[j][b] == (b == a ? -oc[i][b] : oc[i][b]));
+                if (ok) omir[a][i] = j;
+            }
+        }
+    otab_ready = 1;
+}
+
+/* ---- exported lattice description (so the tests can pin it) ---- */
+int oracle_lattice(int *c /* 19*3 */, double *w /* 19 */, int *opp /* 19 */)
+{
+    tables();
+    for (int i = 0; i < ORQ; ++i) {
+        for (int a = 0; a < 3; ++a) c[3 * i + a] = oc[i][a];
+        w[i] = ow[i];
+        opp[i] = oopp[i];
+    }
+    return ORQ;
+}
+
+/* ---- D.4: second-order Hermite equilibrium ---- */
+void oracle_equilibrium(double rho, const double u[3], double feq[ORQ])
+{
+    tables();
+    const double cs2 = 1.0 / 3.0;
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < ORQ; ++i) {
+        const double cu = oc[i][0] * u[0] + oc[i][1] * u[1] + oc[i][2] * u[2];
+        feq[i] = ow[i] * rho * (1.0 + cu / cs2 + cu * cu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2));
+    }
+}
+
+/* ---- D.11: closed-form effective relaxation time ---- */
+double oracle_tau_eff(double tau, double C, double Q, double rho)
+{
+    const double cs2 = 1.0 / 3.0, Delta = 1.0;
+    return 0.5 * (tau + sqrt(tau * tau + 2.0 * (C * Delta) * (C * Delta) * Q / (rho * cs2 * cs2)));
+}
+
+/* ---- one cell: moments, equilibrium, LES closure, BGK (+ Guo source) ----
+ * f:     pre-collision populations (post-stream)
+ * force: body-force density (may be NULL)
+ * out:   post-collision populations; q_out / tau_out optional diagnostics */
+void oracle_collide(const double f[ORQ], double tau, double C, const double *force, double out[ORQ],
+                    double *q_out, double *tau_out)
+{
+    tables();
+    const double cs2 = 1.0 / 3.0;
+    double F[3] = {0.0, 0.0, 0.0};
+    if (force) { F[0] = force[0]; F[1] = force[1]; F[2] = force[2]; }
+
+    /* D.1 */
+    double rho = 0.0, m[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < ORQ; ++i) {
+        rho += f[i];
+        for (int a = 0; a < 3; ++a) m[a] += oc[i][a] * f[i];
+    }
+    /* Guo: the velocity carries half the force impulse */
+    double u[3];
+    for (int a = 0; a < 3; ++a) u[a] = (m[a] + 0.5 * F[a]) / rho;
+
+    double feq[ORQ];
+    oracle_equilibrium(rho, u, feq);
+
+    /* D.8: full 3x3 non-equilibrium momentum flux */
+    double Pi[3][3] = {{0}};
+    for (int i = 0; i < ORQ; ++i)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) Pi[a][b] += oc[i][a] * oc[i][b] * (f[i] - feq[i]);
+    /* D.10 */
+    double PP = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) PP += Pi[a][b] * Pi[a][b];
+    const double Q = sqrt(2.0 * PP);
+    /* D.11 */
+    const double te = oracle_tau_eff(tau, C, Q, rho);
+
+    /* D.2 with Guo's source term S_i = (1 - 1/(2 tau)) w_i [(c - u)/c_s^2 + (c.u) c / c_s^4] . F */
+    for (int i = 0; i < ORQ; ++i) {
+        double cu = 0.0, cF = 0.0, uF = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            cu += oc[i][a] * u[a];
+            cF += oc[i][a] * F[a];
+            uF += u[a] * F[a];
+        }
+        const double S = (1.0 - 0.5 / te) * ow[i] * ((cF - uF) / cs2 + cu * cF / (cs2 * cs2));
+        out[i] = f[i] - (f[i] - feq[i]) / te + S;
+    }
+    if (q_out) *q_out = Q;
+    if (tau_out) *tau_out = te;
+}
+
+/* ---- cell classification: solid mask wins, then equilibrium-face layers, else fluid ---- */
+int oracle_classify(const uint8_t *solid, int nx, int ny, int nz, const int face[6], uint8_t *kind)
+{
+    const int n[3] = {nx, ny, nz};
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t c = ((size_t)z * ny + y) * nx + x;
+                const int p[3] = {x, y, z};
+                uint8_t k = OR_FLUID;
+                for (int a = 0; a < 3; ++a) {
+                    if (p[a] == 0 && face[2 * a] == OR_INFLOW) k = OR_EQ;
+                    if (p[a] == n[a] - 1 && face[2 * a + 1] == OR_INFLOW) k = OR_EQ;
+                }
+                if (solid[c]) k = OR_SOLID;
+                kind[c] = k;
+            }
+    return 0;
+}
+
+/* ---- inflow profile: L level speeds -> per-cell-height velocity u_b[k][3] ----
+ * L divides nz: equal-height blocks.  Otherwise: linear in height between level centres
+ * (cell k sits at height k + 1/2 above the ground wall, level l is centred at (l + 1/2) nz / L),
+ * held constant beyond the first and last centre.  Direction theta: 0 = +x, counter-clockwise. */
+int oracle_expand_profile(const double *speed, int L, int nz, double theta, double *ub)
+{
+    if (L <= 0 || nz <= 0) return -1;
+    for (int k = 0; k < nz; ++k) {
+        double s;
+        if (nz % L == 0) {
+            s = speed[k / (nz / L)];
+        } else {
+            const double h = k + 0.5;
+            const double pos = h * L / nz - 0.5; /* level-centre coordinate */
+            if (pos <= 0.0) s = speed[0];
+            else if (pos >= L - 1) s = speed[L - 1];
+            else {
+                const int l = (int)floor(pos);
+                const double t = pos - l;
+                s = (1.0 - t) * speed[l] + t * speed[l + 1];
+            }
+        }
+        ub[3 * k + 0] = s * cos(theta);
+        ub[3 * k + 1] = s * sin(theta);
+        ub[3 * k + 2] = 0.0;
+    }
+    return 0;
+}
+
+/* ---- initial state: F = f^eq(rho, u) per cell ----
+ * rho, u may be NULL (rho = 1, u = u_b(z)).  Equilibrium cells take f^eq(rho_b, u_b(z)); solid 0. */
+int oracle_init(double *F, const uint8_t *kind, int nx, int ny, int nz, const double *rho,
+                const double *u, const double *ub, double rho_b)
+{
+    tables();
+    const size_t N = (size_t)nx * ny * nz;
+    for (size_t c = 0; c < N; ++c) {
+        const int z = (int)(c / ((size_t)nx * ny));
+        double feq[ORQ];
+        if (kind[c] == OR_SOLID) {
+            for (int i = 0; i < ORQ; ++i) F[i * N + c] = 0.0;
+            continue;
+        }
+        if (kind[c] == OR_EQ) {
+            oracle_equilibrium(rho_b, ub + 3 * z, feq);
+        } else {
+            double uc[3];
+            for (int a = 0; a < 3; ++a) uc[a] = u ? u[3 * c + a] : ub[3 * z + a];
+            oracle_equilibrium(rho ? rho[c] : 1.0, uc, feq);
+        }
+        for (int i = 0; i < ORQ; ++i) F[i * N + c] = feq[i];
+    }
+    return 0;
+}
+
+/* ---- gather rule for the incoming population i of a fluid cell p (D.3 + boundary rules) ----
+ * returns F*_d(s) from the previous post-collision state, or the bounced-back F*_opp(i)(p). */
+static double gather(const double *Fin, const uint8_t *kind, const int n[3], size_t N,
+                     const int face[6], const int p[3], int i)
+{
+    int s[3];
+    int d = i;
+    for (int a = 0; a < 3; ++a) s[a] = p[a] - oc[i][a];
+    const size_t self = ((size_t)p[2] * n[1] + p[1]) * n[0] + p[0];
+
+    /* a no-slip face on any out-of-range axis: halfway bounce-back from the cell itself */
+    for (int a = 0; a < 3; ++a) {
+        if (s[a] < 0 && face[2 * a] == OR_NOSLIP) return Fin[(size_t)oopp[i] * N + self];
+        if (s[a] >= n[a] && face[2 * a + 1] == OR_NOSLIP) return Fin[(size_t)oopp[i] * N + self];
+    }
+    /* resolve the remaining out-of-range axes one at a time */
+    for (int a = 0; a < 3; ++a) {
+        if (s[a] >= 0 && s[a] < n[a]) continue;
+        const int hi = s[a] >= n[a];
+        const int kindf = face[2 * a + hi];
+        if (kindf == OR_PERIODIC) {
+            s[a] = hi ? s[a] - n[a] : s[a] + n[a];
+        } else if (kindf == OR_FREESLIP) {
+            s[a] = hi ? n[a] - 1 : 0;
+            d = omir[a][d];
+        } else { /* outflow (zero-gradient) and, unreachably for fluid cells, equilibrium faces */
+            s[a] = hi ? n[a] - 1 : 0;
+        }
+    }
+    const size_t src = ((size_t)s[2] * n[1] + s[1]) * n[0] + s[0];
+    if (kind[src] == OR_SOLID) return Fin[(size_t)oopp[i] * N + self];
+    return Fin[(size_t)d * N + src];
+}
+
+/* ---- one full time step over z-planes [z0, z1) (pass 0, nz for the whole lattice) ----
+ * Fin:  post-collision state at step t (19 x N, population-major, x fastest)
+ * Fout: post-collision state at step t+1
+ * q_out, tau_out: optional per-cell Q and tau_eff of the step (fluid cells; NaN elsewhere) */
+int oracle_step(const double *Fin, double *Fout, const uint8_t *kind, int nx, int ny, int nz,
+                const int face[6], const double *ub, double rho_b, double tau, double C,
+                const double *force, int z0, int z1, double *q_out, double *tau_out)
+{
+    tables();
+    const int n[3] = {nx, ny, nz};
+    const size_t N = (size_t)nx * ny * nz;
+    if (z0 < 0) z0 = 0;
+    if (z1 > nz) z1 = nz;
+#pragma omp parallel for schedule(static)
+    for (int z = z0; z < z1; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t c = ((size_t)z * ny + y) * nx + x;
+                double f[ORQ], out[ORQ];
+                double q = NAN, te = NAN;
+                if (kind[c] == OR_SOLID) {
+                    for (int i = 0; i < ORQ; ++i) out[i] = 0.0;
+                } else if (kind[c] == OR_EQ) {
+                    oracle_equilibrium(rho_b, ub + 3 * z, out);
+                } else {
+                    const int p[3] = {x, y, z};
+                    for (int i = 0; i < ORQ; ++i) f[i] = gather(Fin, kind, n, N, face, p, i);
+                    oracle_collide(f, tau, C, force, out, &q, &te);
+                }
+                for (int i = 0; i < ORQ; ++i) Fout[(size_t)i * N + c] = out[i];
+                if (q_out) q_out[c] = q;
+                if (tau_out) tau_out[c] = te;
+            }
+    return 0;
+}
+
+/* ---- observed macroscopic fields of a post-collision state ----
+ * fluid: rho = sum F*, u = (sum c F* - F/2) / rho (Guo: sum c F* = rho u + F/2 after collision)
+ * equilibrium cells: (rho_b, u_b(z)); solid: rho = 0, u = 0. */
+int oracle_macros(const double *F, const uint8_t *kind, int nx, int ny, int nz, const double *ub,
+                  double rho_b, const double *force, double *rho, double *u)
+{
+    tables();
+    const size_t N = (size_t)nx * ny * nz;
+#pragma omp parallel for schedule(static)
+    for (long long cc = 0; cc < (long long)N; ++cc) {
+        const size_t c = (size_t)cc;
+        const int z = (int)(c / ((size_t)nx * ny));
+        if (kind[c] == OR_SOLID) {
+            rho[c] = 0.0;
+            u[3 * c] = u[3 * c + 1] = u[3 * c + 2] = 0.0;
+            continue;
+        }
+        if (kind[c] == OR_EQ) {
+            rho[c] = rho_b;
+            for (int a = 0; a < 3; ++a) u[3 * c + a] = ub[3 * z + a];
+            continue;
+        }
+        double r = 0.0, m[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < ORQ; ++i) {
+            const double v = F[(size_t)i * N + c];
+            r += v;
+            for (int a = 0; a < 3; ++a) m[a] += oc[i][a] * v;
+        }
+        rho[c] = r;
+        for (int a = 0; a < 3; ++a) u[3 * c + a] = (m[a] - 0.5 * (force ? force[a] : 0.0)) / r;
+    }
+    return 0;
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,188 @@
+"""FP64 CPU oracle -- Python wrapper around ``lbm_oracle.c`` (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+this module.  The product library (``paper_2607_04516_b300``) never imports it and has no path
+that falls back to it.
+
+Array conventions (all float64, C-contiguous):
+    F     (19, nz, ny, nx)   post-collision populations, oracle direction order (``lattice()``)
+    kind  (nz, ny, nx) u8    0 fluid, 1 solid, 2 equilibrium-boundary cell
+    ub    (nz, 3)            equilibrium-boundary velocity per cell height
+    u     (nz, ny, nx, 3)    velocity
+Face kinds are given by name, in the order x-, x+, y-, y+, z-, z+:
+    'periodic' | 'inflow' | 'outflow' | 'freeslip' | 'noslip'
+
+The paper passages each function follows are cited in ``lbm_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+
+FACE_CODES = {"periodic": 0, "inflow": 1, "outflow": 2, "freeslip": 3, "noslip": 4}
+FLUID, SOLID, EQ = 0, 1, 2
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc + OpenMP into ``oracle/_build/liboracle.so``."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        D = ctypes.c_double
+        L.oracle_lattice.argtypes = [P, P, P]
+        L.oracle_lattice.restype = I
+        L.oracle_equilibrium.argtypes = [D, P, P]
+        L.oracle_equilibrium.restype = None
+        L.oracle_tau_eff.argtypes = [D, D, D, D]
+        L.oracle_tau_eff.restype = D
+        L.oracle_collide.argtypes = [P, D, D, P, P, P, P]
+        L.oracle_collide.restype = None
+        L.oracle_classify.argtypes = [P, I, I, I, P, P]
+        L.oracle_classify.restype = I
+        L.oracle_expand_profile.argtypes = [P, I, I, D, P]
+        L.oracle_expand_profile.restype = I
+        L.oracle_init.argtypes = [P, P, I, I, I, P, P, P, D]
+        L.oracle_init.restype = I
+        L.oracle_step.argtypes = [P, P, P, I, I, I, P, P, D, D, D, P, I, I, P, P]
+        L.oracle_step.restype = I
+        L.oracle_macros.argtypes = [P, P, I, I, I, P, D, P, P, P]
+        L.oracle_macros.restype = I
+        L.oracle_num_threads.argtypes = []
+        L.oracle_num_threads.restype = I
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data
+
+
+def _faces(faces) -> np.ndarray:
+    return np.array([FACE_CODES[f] for f in faces], dtype=np.int32)
+
+
+def lattice():
+    """(c (19,3) int, w (19,) float, opp (19,) int) in the oracle's direction order."""
+    c = np.zeros((19, 3), np.int32)
+    w = np.zeros(19, np.float64)
+    opp = np.zeros(19, np.int32)
+    lib().oracle_lattice(_p(c), _p(w), _p(opp))
+    return c.astype(np.int64), w, opp.astype(np.int64)
+
+
+def equilibrium(rho: float, u) -> np.ndarray:
+    u = np.ascontiguousarray(u, np.float64)
+    out = np.zeros(19, np.float64)
+    lib().oracle_equilibrium(float(rho), _p(u), _p(out))
+    return out
+
+
+def tau_eff(tau: float, C: float, Q: float, rho: float) -> float:
+    return lib().oracle_tau_eff(float(tau), float(C), float(Q), float(rho))
+
+
+def collide(f, tau: float, C: float, force=None):
+    """One-cell collision; returns (f*, Q, tau_eff)."""
+    f = np.ascontiguousarray(f, np.float64)
+    out = np.zeros(19, np.float64)
+    q = ctypes.c_double()
+    te = ctypes.c_double()
+    fz = None if force is None else np.ascontiguousarray(force, np.float64)
+    lib().oracle_collide(_p(f), float(tau), float(C), _p(fz), _p(out),
+                         ctypes.addressof(q), ctypes.addressof(te))
+    return out, q.value, te.value
+
+
+def classify(solid: np.ndarray, faces) -> np.ndarray:
+    solid = np.ascontiguousarray(solid, np.uint8)
+    nz, ny, nx = solid.shape
+    kind = np.zeros_like(solid)
+    lib().oracle_classify(_p(solid), nx, ny, nz, _p(_faces(faces)), _p(kind))
+    return kind
+
+
+def expand_profile(speed, nz: int, theta: float) -> np.ndarray:
+    speed = np.ascontiguousarray(speed, np.float64)
+    ub = np.zeros((nz, 3), np.float64)
+    rc = lib().oracle_expand_profile(_p(speed), len(speed), nz, float(theta), _p(ub))
+    if rc != 0:
+        raise ValueError("bad profile")
+    return ub
+
+
+def init(kind: np.ndarray, ub: np.ndarray, rho=None, u=None, rho_b: float = 1.0) -> np.ndarray:
+    nz, ny, nx = kind.shape
+    F = np.zeros((19, nz, ny, nx), np.float64)
+    rho = None if rho is None else np.ascontiguousarray(rho, np.float64)
+    u = None if u is None else np.ascontiguousarray(u, np.float64)
+    ub = np.ascontiguousarray(ub, np.float64)
+    lib().oracle_init(_p(F), _p(np.ascontiguousarray(kind, np.uint8)), nx, ny, nz,
+                      _p(rho), _p(u), _p(ub), float(rho_b))
+    return F
+
+
+def step(F: np.ndarray, kind: np.ndarray, faces, ub: np.ndarray, tau: float, C: float,
+         force=None, rho_b: float = 1.0, z0: int = 0, z1: int | None = None,
+         out: np.ndarray | None = None, diag: bool = False):
+    """One time step (pull form).  Returns F_next, or (F_next, Q, tau_eff) if ``diag``."""
+    nz, ny, nx = kind.shape
+    if out is None:
+        out = np.zeros_like(F)
+    fz = None if force is None else np.ascontiguousarray(force, np.float64)
+    q = te = None
+    if diag:
+        q = np.zeros((nz, ny, nx), np.float64)
+        te = np.zeros((nz, ny, nx), np.float64)
+    lib().oracle_step(_p(F), _p(out), _p(kind), nx, ny, nz, _p(_faces(faces)),
+                      _p(np.ascontiguousarray(ub, np.float64)), float(rho_b), float(tau), float(C),
+                      _p(fz), int(z0), int(nz if z1 is None else z1), _p(q), _p(te))
+    return (out, q, te) if diag else out
+
+
+def run(F: np.ndarray, nsteps: int, *args, **kw) -> np.ndarray:
+    """``nsteps`` steps with two ping-pong buffers; returns the final state."""
+    a = F.copy()
+    b = np.empty_like(F)
+    for _ in range(nsteps):
+        step(a, *args, out=b, **kw)
+        a, b = b, a
+    return a
+
+
+def macros(F: np.ndarray, kind: np.ndarray, ub: np.ndarray, rho_b: float = 1.0, force=None):
+    nz, ny, nx = kind.shape
+    rho = np.zeros((nz, ny, nx), np.float64)
+    u = np.zeros((nz, ny, nx, 3), np.float64)
+    fz = None if force is None else np.ascontiguousarray(force, np.float64)
+    lib().oracle_macros(_p(F), _p(kind), nx, ny, nz, _p(np.ascontiguousarray(ub, np.float64)),
+                        float(rho_b), _p(fz), _p(rho), _p(u))
+    return rho, u
+
+
+def num_threads() -> int:
+    return lib().oracle_num_threads()

@@ -1,0 +1,223 @@
+"""Seeded synthetic inputs: geometry, inflow level speeds, initial velocity fields.
+
+This module produces INPUTS only -- solid masks, face kinds, per-level inflow speeds and explicit
+initial velocity fields -- and holds none of the solver's arithmetic.  The CUDA path and the FP64
+oracle are both fed from it; neither is imported here.
+
+The paper's own inputs (3D-GloBFP building footprints, NASADEM terrain, Doppler-lidar boundary
+winds; Sec. 3) are not available, so every workload is synthetic, shaped like the paper's: a 5 m
+lattice over a kilometre-scale urban patch with N_cell of order 1e7-1e8 (Sec. 3, baseline case),
+buildings as voxel solids on a no-slip ground, an observation-like sheared inflow profile.
+
+Conventions: arrays are (nz, ny, nx) with x fastest in memory; a height level k is the cell
+whose centre sits k + 1/2 above the ground wall (the wall lies half a spacing below the first
+cell, App. D, bounce-back paragraph).  Face kinds in the order x-, x+, y-, y+, z-, z+:
+'periodic' | 'inflow' | 'outflow' | 'freeslip' | 'noslip'.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Case:
+    """One synthetic workload: geometry, faces, model constants, inflow levels, initial field."""
+    name: str
+    solid: np.ndarray                 # (nz, ny, nx) uint8, 1 = solid
+    faces: tuple                      # 6 face kinds
+    tau: float
+    cs: float                         # Smagorinsky constant C
+    speed: np.ndarray                 # inflow speed per level (L levels)
+    theta: float                      # inflow direction [rad], 0 = +x, counter-clockwise
+    u0: np.ndarray | None = None      # (nz, ny, nx, 3) initial velocity (None: profile)
+    rho0: np.ndarray | None = None    # (nz, ny, nx) initial density (None: 1)
+    force: tuple | None = None        # uniform body-force density (Guo forcing), lattice units
+    rho_b: float = 1.0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def shape(self):
+        return self.solid.shape
+
+    @property
+    def dims(self):
+        nz, ny, nx = self.solid.shape
+        return nx, ny, nz
+
+
+# ----------------------------------------------------------------------------- inflow levels
+def log_law_levels(nz: int, u_ref: float, z_ref: float, z0: float) -> np.ndarray:
+    """Neutral log-law speed at each cell height k + 1/2: u_ref ln(z/z0) / ln(z_ref/z0)."""
+    z = np.arange(nz) + 0.5
+    return u_ref * np.log(z / z0) / math.log(z_ref / z0)
+
+
+def power_law_levels(nz: int, u_ref: float, z_ref: float, alpha: float) -> np.ndarray:
+    """Power-law speed at each cell height k + 1/2: u_ref (z / z_ref)^alpha."""
+    z = np.arange(nz) + 0.5
+    return u_ref * (z / z_ref) ** alpha
+
+
+def direction_from_seed(seed: int) -> float:
+    """Inflow direction uniform in [0, 360) degrees, returned in radians."""
+    return math.radians(float(np.random.default_rng(seed).uniform(0.0, 360.0)))
+
+
+def faces_for_direction(theta: float, bottom: str = "noslip", top: str = "freeslip") -> tuple:
+    """A lateral face is an inflow face when the wind blows into the domain through it
+    (u . n_in > 0), an outflow face otherwise."""
+    cx, cy = math.cos(theta), math.sin(theta)
+    eps = 1e-12
+    return ("inflow" if cx > eps else "outflow", "inflow" if cx < -eps else "outflow",
+            "inflow" if cy > eps else "outflow", "inflow" if cy < -eps else "outflow",
+            bottom, top)
+
+
+# ----------------------------------------------------------------------------- initial fields
+def profile_field(speed_per_cell: np.ndarray, theta: float, shape) -> np.ndarray:
+    """Velocity field equal to the level speed of each cell height, along theta (L == nz)."""
+    nz, ny, nx = shape
+    assert len(speed_per_cell) == nz
+    u = np.zeros((nz, ny, nx, 3), np.float64)
+    u[..., 0] = (speed_per_cell * math.cos(theta))[:, None, None]
+    u[..., 1] = (speed_per_cell * math.sin(theta))[:, None, None]
+    return u
+
+
+def perturb(u: np.ndarray, solid: np.ndarray, amp: float, seed: int) -> np.ndarray:
+    """u + amp * xi, xi ~ U[-1, 1]^3 per cell and component (PCG64 stream ``seed``); solids 0."""
+    xi = np.random.default_rng(seed).uniform(-1.0, 1.0, size=u.shape)
+    out = u + amp * xi
+    out[solid.astype(bool)] = 0.0
+    return out
+
+
+# ----------------------------------------------------------------------------- geometry
+def cube_case(nx: int = 64, ny: int = 64, nz: int = 32, seed: int = 0, tau: float = 0.52,
+              cs: float = 0.16, noise: float = 0.01) -> Case:
+    """Single cubical building 8 x 8 x 16 cells centred in a 64 x 64 x 32 lattice; log-law
+    inflow along +x (u_ref 0.05 at z = 32, z0 = 0.1); zero-gradient outflow; periodic in y;
+    no-slip ground; free-slip top; initial velocity = profile + 1% u_ref uniform noise."""
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    cx0, cy0 = nx // 2 - 4, ny // 2 - 4
+    solid[0:min(16, nz - 1), cy0:cy0 + 8, cx0:cx0 + 8] = 1
+    speed = log_law_levels(nz, 0.05, 32.0, 0.1)
+    faces = ("inflow", "outflow", "periodic", "periodic", "noslip", "freeslip")
+    u0 = perturb(profile_field(speed, 0.0, solid.shape), solid, noise * 0.05, seed)
+    return Case("cube", solid, faces, tau, cs, speed, 0.0, u0=u0,
+                meta={"seed": seed, "noise": noise})
+
+
+def city_mask(nx: int, ny: int, nz: int, seed: int, plan_fraction: float = 0.35,
+              side_min: int = 2, side_max: int = 12, margin: int = 8, gap: int = 1,
+              h_median: float = 6.0, h_sigma: float = 0.6, h_max: int = 50,
+              max_attempts: int = 1_000_000) -> tuple[np.ndarray, dict]:
+    """Box city by seeded dart throwing: footprints with sides U{side_min..side_max} (x and y
+    independent), rejected within ``gap`` cells of another footprint or within ``margin`` cells
+    of a lateral face, until the plan-area fraction reaches ``plan_fraction``; heights
+    round(exp(ln h_median + h_sigma N(0,1))) clamped to [1, min(h_max, nz - 2)]."""
+    rng = np.random.default_rng(seed)
+    occ = np.zeros((ny, nx), bool)
+    height = np.zeros((ny, nx), np.int32)
+    target = plan_fraction * nx * ny
+    area = 0
+    attempts = 0
+    placed = 0
+    hcap = max(1, min(h_max, nz - 2))
+    batch = 4096
+    while area < target and attempts < max_attempts:
+        sx = rng.integers(side_min, side_max + 1, size=batch)
+        sy = rng.integers(side_min, side_max + 1, size=batch)
+        ux = rng.random(batch)
+        uy = rng.random(batch)
+        hs = rng.standard_normal(batch)
+        for b in range(batch):
+            attempts += 1
+            w, d = int(sx[b]), int(sy[b])
+            span_x = nx - 2 * margin - w
+            span_y = ny - 2 * margin - d
+            if span_x < 0 or span_y < 0:
+                continue
+            x0 = margin + int(ux[b] * (span_x + 1))
+            y0 = margin + int(uy[b] * (span_y + 1))
+            if occ[max(0, y0 - gap):y0 + d + gap, max(0, x0 - gap):x0 + w + gap].any():
+                continue
+            h = int(round(math.exp(math.log(h_median) + h_sigma * hs[b])))
+            h = min(max(h, 1), hcap)
+            occ[y0:y0 + d, x0:x0 + w] = True
+            height[y0:y0 + d, x0:x0 + w] = h
+            area += w * d
+            placed += 1
+            if area >= target or attempts >= max_attempts:
+                break
+    z = np.arange(nz)[:, None, None]
+    solid = (z < height[None, :, :]).astype(np.uint8)
+    info = {"buildings": placed, "attempts": attempts, "plan_fraction": area / (nx * ny),
+            "solid_fraction": float(solid.mean())}
+    return solid, info
+
+
+def city_case(nx: int = 400, ny: int = 400, nz: int = 80, seed: int = 1, dir_seed: int | None = None,
+              tau: float = 0.505, cs: float = 0.16, u_ref: float = 0.06, z_ref: float = 60.0,
+              alpha: float = 0.25, noise: float = 0.01) -> Case:
+    """Synthetic city on a 5 m lattice (400 x 400 x 80 = 2 km x 2 km x 400 m by default):
+    power-law inflow from a seeded direction; lateral faces inflow/outflow by the wind
+    direction; free-slip top; no-slip ground."""
+    solid, info = city_mask(nx, ny, nz, seed)
+    theta = direction_from_seed(seed if dir_seed is None else dir_seed)
+    speed = power_law_levels(nz, u_ref, z_ref, alpha)
+    faces = faces_for_direction(theta)
+    u0 = perturb(profile_field(speed, theta, solid.shape), solid, noise * u_ref, seed + 1000)
+    return Case(f"city{nx}x{ny}x{nz}", solid, faces, tau, cs, speed, theta, u0=u0,
+                meta={"seed": seed, **info})
+
+
+def taylor_green_case(n: int = 32, U0: float = 0.01, tau: float = 0.8, cs: float = 0.0,
+                      nz: int | None = None) -> Case:
+    """2D Taylor-Green vortex extruded along z in a fully periodic box:
+    u = -U0 cos(kx) sin(ky), v = U0 sin(kx) cos(ky), k = 2 pi / n, at cell centres."""
+    nz = n if nz is None else nz
+    k = 2.0 * math.pi / n
+    x = np.arange(n) + 0.0
+    X, Y = np.meshgrid(x, x, indexing="xy")          # (ny, nx)
+    u = np.zeros((nz, n, n, 3))
+    u[..., 0] = (-U0 * np.cos(k * X) * np.sin(k * Y))[None]
+    u[..., 1] = (U0 * np.sin(k * X) * np.cos(k * Y))[None]
+    solid = np.zeros((nz, n, n), np.uint8)
+    faces = ("periodic",) * 6
+    return Case(f"tg{n}", solid, faces, tau, cs, np.zeros(nz), 0.0, u0=u,
+                meta={"U0": U0, "k": k})
+
+
+def channel_case(nz: int = 16, nxy: int = 4, force: float = 1e-6, tau: float = 0.5 + math.sqrt(3 / 16),
+                 cs: float = 0.0) -> Case:
+    """Plane channel between no-slip walls at z = -1/2 and z = nz - 1/2, periodic in x and y,
+    driven by a uniform body force along +x; starts from rest."""
+    solid = np.zeros((nz, nxy, nxy), np.uint8)
+    faces = ("periodic", "periodic", "periodic", "periodic", "noslip", "noslip")
+    u0 = np.zeros((nz, nxy, nxy, 3))
+    return Case(f"channel{nz}", solid, faces, tau, cs, np.zeros(nz), 0.0, u0=u0,
+                force=(force, 0.0, 0.0))
+
+
+def random_small_case(nx: int, ny: int, nz: int, faces, seed: int, solid_fraction: float = 0.1,
+                      u_amp: float = 0.05, tau: float = 0.6, cs: float = 0.16,
+                      theta: float = 0.3, margin: int = 1) -> Case:
+    """Tiny lattice with scattered solid cells (kept ``margin`` cells off the lateral faces),
+    random initial velocity and density -- for brute-force cross-checks of the boundary logic."""
+    rng = np.random.default_rng(seed)
+    solid = (rng.random((nz, ny, nx)) < solid_fraction).astype(np.uint8)
+    if margin > 0:
+        solid[:, :, :margin] = 0
+        solid[:, :, nx - margin:] = 0
+        solid[:, :margin, :] = 0
+        solid[:, ny - margin:, :] = 0
+    u0 = rng.uniform(-u_amp, u_amp, size=(nz, ny, nx, 3))
+    u0[solid.astype(bool)] = 0.0
+    rho0 = 1.0 + rng.uniform(-0.01, 0.01, size=(nz, ny, nx))
+    speed = u_amp * (0.5 + 0.5 * rng.random(nz))
+    return Case(f"rand{nx}x{ny}x{nz}", solid, tuple(faces), tau, cs, speed, theta, u0=u0,
+                rho0=rho0)
