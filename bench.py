@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""LBM-LES throughput on one B300: GLUPS and fraction of the HBM roofline.
+
+Workload (default): the synthetic 5 m city, 400 x 400 x 80 = 12.8M cells (2 km x 2 km x 400 m),
+Poisson-disk box buildings to a plan-area fraction of 0.35, power-law inflow (alpha 0.25,
+u_ref 0.06 at z = 60) from a seeded direction, tau = 0.505, Smagorinsky C = 0.16, FP32 populations.
+One benchmark step = one fused D3Q19 stream-collide time step over the whole lattice (the whole
+hot path).  The state (1.95 GB in FP32) is 15x the 126 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--store f32|f16s|bf16s]
+                    [--workload city400|city256|city1000|cube] [--impl ours|reference]
+
+Prints ONE JSON line on rank 0.  Multi-GPU (torchrun): every rank runs an independent replica of
+the workload (the single-domain path has no exchange step here), value = all ranks' cell updates
+over the slowest rank's time, "scaling": "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "city400": dict(nx=400, ny=400, nz=80, seed=1),
+    "city256": dict(nx=256, ny=256, nz=64, seed=1),
+    "city1000": dict(nx=1000, ny=1000, nz=160, seed=1),
+    "cube": None,
+}
+METRIC = "LBM-LES GLUPS & % HBM roofline, FP32 vs 16-bit storage"
+STORE_BYTES = {"f32": 4, "f16s": 2, "bf16s": 2}
+DTYPE_NAME = {"f32": "f32", "f16s": "f16-storage/f32-math", "bf16s": "bf16-storage/f32-math"}
+SOURCES = ["paper_2607_04516_b300/csrc/lbm_device.cuh", "paper_2607_04516_b300/csrc/lbm_cell.cuh",
+           "paper_2607_04516_b300/csrc/lbm_kernels.cu"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=19000)
+    ap.add_argument("--warmup", type=int, default=1000)
+    ap.add_argument("--store", default="f32", choices=list(STORE_BYTES))
+    ap.add_argument("--workload", default="city400", choices=list(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variants", default="f16s,bf16s",
+                    help="extra storage kinds timed after the main measurement ('' = none)")
+    ap.add_argument("--e2e-steps", type=int, default=1000)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def make_case(workload):
+    from paper_2607_04516_b300 import synth
+    if workload == "cube":
+        return synth.cube_case()
+    w = WORKLOADS[workload]
+    return synth.city_case(nx=w["nx"], ny=w["ny"], nz=w["nz"], seed=w["seed"])
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for p in SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def recorded_traffic(kernel: str, workload: str, store: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}_{store}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    s = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    if not m or not s or s.group(1) != source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, smax, reasons = [], [], set()
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("LBM_BENCH_BACKEND") != "gloo" else "gloo")
+    return rank, world
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- our arm
+def time_steps(dom, K: int, W: int, world: int, clock_id: str | None):
+    """W untimed steps, then K steps with a CUDA event before/after every launch on the domain's
+    stream (the library enqueues on the stream the domain was created with)."""
+    import torch
+    dom.step(W)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    sampler = ClockSampler(clock_id) if clock_id else None
+    t_wall = time.perf_counter()
+    parity0 = dom.steps_done % 2
+    evs[0].record(dom.stream)
+    for k in range(K):
+        dom.step(1)
+        evs[k + 1].record(dom.stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop() if sampler else None
+    barrier(world)
+    total_ms = evs[0].elapsed_time(evs[K])
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(K)]
+    # launch k is the neighbour kernel when (parity0 + k) is even
+    nb = [t for k, t in enumerate(per) if (parity0 + k) % 2 == 0]
+    lc = [t for k, t in enumerate(per) if (parity0 + k) % 2 == 1]
+    return total_ms, nb, lc, wall, clocks
+
+
+def e2e_glups(dom, case, steps: int, world: int):
+    """Public-API loop with host buffers: per step the inflow profile goes host -> device
+    (lbm_set_inflow_profile from pinned host memory), one lbm_step, and 8 virtual-lidar columns x
+    10 heights come back device -> pinned host (lbm_sample_columns + copy + stream sync)."""
+    import numpy as np
+    import torch
+    nz, ny, nx = case.shape
+    speed = torch.tensor(case.speed, dtype=torch.float32).pin_memory()
+    rng = np.random.default_rng(7)
+    fluid_cols = [(int(x), int(y)) for x, y in zip(rng.integers(16, nx - 16, 64), rng.integers(16, ny - 16, 64))
+                  if not case.solid[0, y, x]][:8]
+    ij = torch.tensor(fluid_cols, dtype=torch.int32, device=dom.device)
+    kk = torch.tensor([min(nz - 1, 4 * (i + 1)) for i in range(10)], dtype=torch.int32, device=dom.device)
+    out_d = torch.empty((len(fluid_cols), 10, 4), dtype=torch.float32, device=dom.device)
+    out_h = torch.empty(out_d.shape, dtype=torch.float32).pin_memory()
+    from paper_2607_04516_b300 import lbm
+    speed_np = speed.numpy()
+    for _ in range(10):
+        dom.set_inflow_profile(speed_np, case.theta)
+        dom.step(1)
+        dom.sample_columns(ij, kk, out_d)
+        out_h.copy_(out_d, non_blocking=True)
+        dom.stream.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        dom.set_inflow_profile(speed_np, case.theta)
+        dom.step(1)
+        lbm.lbm_sample_columns(dom.dom, ij, kk, out_d)
+        out_h.copy_(out_d, non_blocking=True)
+        dom.stream.synchronize()
+    dt = time.perf_counter() - t0
+    dt = max_over_ranks(dt, world)
+    return (case.solid.size * steps * world / dt / 1e9, 4 * len(speed_np), out_h.numel() * 4,
+            dt * 1e3 / steps)
+
+
+def cpu_baseline(case, seconds: float):
+    """The FP64 oracle as it stands, on all host cores, over whole-lattice steps of this workload."""
+    import numpy as np
+    from oracle import oracle as orc
+    kind = orc.classify(case.solid, case.faces)
+    ub = orc.expand_profile(case.speed.astype(np.float32).astype(np.float64), case.shape[0],
+                            float(np.float32(case.theta)))
+    F = orc.init(kind, ub, None, None if case.u0 is None else case.u0)
+    out = np.empty_like(F)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        orc.step(F, kind, case.faces, ub, case.tau, case.cs, out=out)
+        F, out = out, F
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    cells = case.solid.size
+    return {"value": cells * steps / dt / 1e9, "unit": "GLUPS", "cores": orc.num_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} full time steps of the {case.shape[2]}x{case.shape[1]}x{case.shape[0]} "
+                      f"workload ({cells} cells) in {dt:.1f} s, FP64, OpenMP over z-planes"}
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_2607_04516_b300 import build as lbuild
+    from paper_2607_04516_b300 import lbm
+
+    if rank == 0:
+        lbuild.build()
+    barrier(world)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    case = make_case(args.workload)
+    nz, ny, nx = case.shape
+    N = nx * ny * nz
+    nonsolid = int(N - case.solid.sum())
+    props = torch.cuda.get_device_properties(local)
+    clock_id = getattr(props, "uuid", None)
+    clock_id = f"GPU-{clock_id}" if clock_id is not None and not str(clock_id).startswith("GPU-") else (
+        str(clock_id) if clock_id is not None else str(local))
+
+    def build_domain(store):
+        dom = lbm.Domain(case.solid, case.faces, case.tau, case.cs, store)
+        dom.set_inflow_profile(case.speed.astype(np.float32), case.theta)
+        dom.init_fields(None, None if case.u0 is None else case.u0.astype(np.float32))
+        return dom
+
+    dom = build_domain(args.store)
+    total_ms, nb, lc, wall, clocks = time_steps(dom, args.steps, args.warmup, world,
+                                                clock_id if rank == 0 else None)
+    total_ms = max_over_ranks(total_ms, world)
+    diag = dom.diagnostics()
+    value = N * args.steps * world / (total_ms / 1e3) / 1e9
+
+    sb = STORE_BYTES[args.store]
+    alg_bytes = nonsolid * 2 * 19 * sb + N            # read + write every population, + flags
+    peak, peak_src = measured_peaks()
+    kernels = {"k_step_neighbor": nb, "k_step_local": lc}
+    stats = {}
+    for name, ts in kernels.items():
+        if ts:
+            avg = sum(ts) / len(ts)
+            stats[name] = {"launches": len(ts), "avg_ms": avg, "total_ms": sum(ts),
+                           "achieved_gbs": alg_bytes / (avg / 1e3) / 1e9}
+    dominant = max(stats, key=lambda k: stats[k]["total_ms"])
+    ach = stats[dominant]["achieved_gbs"]
+    traffic = recorded_traffic(dominant, args.workload, args.store)
+
+    e2e_val, h2d, d2h, e2e_ms = e2e_glups(dom, case, args.e2e_steps, world)
+    del dom
+    torch.cuda.empty_cache()
+
+    variants = {}
+    for st in [v for v in args.variants.split(",") if v and v != args.store]:
+        d2 = build_domain(st)
+        t_ms, nb2, lc2, _, _ = time_steps(d2, max(200, args.steps // 4), min(args.warmup, 200), world, None)
+        t_ms = max_over_ranks(t_ms, world)
+        K2 = max(200, args.steps // 4)
+        g2 = N * K2 * world / (t_ms / 1e3) / 1e9
+        ab2 = nonsolid * 2 * 19 * STORE_BYTES[st] + N
+        avg2 = max(sum(nb2) / len(nb2), sum(lc2) / len(lc2))
+        variants[st] = {"glups": g2, "vs_f32": g2 / value if args.store == "f32" else None,
+                        "frac_hbm_dominant": ab2 / (avg2 / 1e3) / 1e9 / peak}
+        del d2
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        return None
+    cpu = None if args.no_cpu_baseline else cpu_baseline(case, args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[args.store], "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {nx}x{ny}x{nz} synthetic city, 5 m cells" if args.workload != "cube"
+                   else "cube 64x64x32", "cells": N, "fluid_cells": nonsolid,
+                   "tau": case.tau, "cs_smag": case.cs, "store": args.store, "faces": list(case.faces),
+                   "inflow_dir_deg": math.degrees(case.theta),
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "state larger than the 126 MB L2 (no flush between steps)"},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": ach / peak, "traffic": traffic, "kernel": dominant,
+                     "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "kernels": stats},
+        "e2e": {"value": e2e_val, "unit": "GLUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "variants": variants,
+        "diagnostics_after": {k: (float(v) if not isinstance(v, int) else v) for k, v in diag.items()},
+        "wall_s_timed": wall,
+    }
+    return line
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The FP64 oracle as it stands on the host cores, same workload and metric; each benchmark
+    step is one oracle time step restricted to a slab of z-planes sized so the whole run ends in
+    about two minutes."""
+    if rank != 0:
+        return None
+    import numpy as np
+    from oracle import oracle as orc
+    case = make_case(args.workload)
+    nz, ny, nx = case.shape
+    kind = orc.classify(case.solid, case.faces)
+    ub = orc.expand_profile(case.speed.astype(np.float32).astype(np.float64), nz, float(np.float32(case.theta)))
+    F = orc.init(kind, ub, None, case.u0)
+    out = np.empty_like(F)
+    t0 = time.perf_counter()
+    orc.step(F, kind, case.faces, ub, case.tau, case.cs, out=out, z0=0, z1=1)
+    plane_s = max(time.perf_counter() - t0, 1e-4)
+    budget = 120.0
+    planes = int(max(1, min(nz, budget / ((args.steps + args.warmup) * plane_s))))
+    z = 0
+    for _ in range(args.warmup):
+        orc.step(F, kind, case.faces, ub, case.tau, case.cs, out=out, z0=z, z1=z + planes)
+        z = (z + planes) % max(1, nz - planes + 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.step(F, kind, case.faces, ub, case.tau, case.cs, out=out, z0=z, z1=z + planes)
+        z = (z + planes) % max(1, nz - planes + 1)
+    dt = time.perf_counter() - t0
+    cells = planes * nx * ny * args.steps
+    val = cells / dt / 1e9
+    sample = (f"each step = one FP64 oracle time step over {planes} z-plane(s) "
+              f"({planes * nx * ny} cells) of the {nx}x{ny}x{nz} workload")
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {nx}x{ny}x{nz} synthetic city, 5 m cells",
+                       "cells": nx * ny * nz, "store": "f64 (oracle)"},
+            "cpu_baseline": {"value": val, "unit": "GLUPS", "cores": orc.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world = dist_init()
+    line = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

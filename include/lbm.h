@@ -1,0 +1,181 @@
+/*
+ * lbm.h -- C ABI of the B300 (sm_103a) LBM-LES urban-wind step.
+ *
+ * One call advances a lattice by n time steps of the fused D3Q19 stream-and-collide update of
+ * the paper's solver (App. D): SRT-BGK collision (Eq. D.2) with the Smagorinsky-Lilly closure
+ * evaluated locally from the non-equilibrium momentum flux (Eqs. D.8-D.11), streaming (Eq. D.3),
+ * mid-grid bounce-back at solid cells and no-slip faces (App. D, last paragraph), equilibrium
+ * velocity boundary cells on inflow faces (Sec. 3, boundary-condition paragraph), zero-gradient
+ * outflow, free-slip and periodic faces, all applied in the same pass over the lattice.
+ *
+ * Conventions shared by every entry point
+ *   - Lattice: nx * ny * nz cells, cell index c = (z * ny + y) * nx + x (x fastest).  z is up;
+ *     the ground wall lies half a spacing below z = 0.  Lattice units (dx = dt = 1).
+ *   - Ownership: the caller owns every device buffer and the CUDA stream.  The library never
+ *     allocates device memory: the whole domain state lives in a caller-provided workspace of
+ *     lbm_workspace_bytes() bytes (e.g. a torch uint8 CUDA tensor).  Host memory for the opaque
+ *     handle comes from malloc.
+ *   - Streams: every call is enqueued on the stream given to lbm_create_domain (a cudaStream_t
+ *     passed as void*, NULL = legacy default stream) and returns without waiting for the GPU,
+ *     except lbm_diagnostics, which synchronises that stream.
+ *   - Errors: every call returns an lbm_status; on failure the domain keeps a message readable
+ *     with lbm_last_error().  Invalid arguments are detected on the host before any launch;
+ *     launch failures return LBM_ECUDA.  No call aborts or traps.
+ *   - Direction order of exported populations (lbm_direction_table): 0 = rest, 1..6 = +x -x +y
+ *     -y +z -z, 7..18 = the twelve face diagonals, opposite directions in pairs (2k-1, 2k).
+ */
+#ifndef LBM_B300_H
+#define LBM_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_domain lbm_domain; /* opaque */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,    /* bad argument (sizes, NULL pointer, face combination, parameter range) */
+    LBM_ENOMEM = -2,    /* workspace smaller than lbm_workspace_bytes(), or host malloc failed */
+    LBM_ECUDA = -3,     /* a CUDA call or kernel launch failed (message holds cudaGetErrorString) */
+    LBM_EUNSTABLE = -4, /* watchdog: non-finite populations found (see lbm_params.watchdog_every) */
+    LBM_ESTATE = -5     /* call not valid in the domain's current state */
+} lbm_status;
+
+/* Face kinds, per face in the order x-, x+, y-, y+, z-, z+.
+ *   PERIODIC    wrap to the opposite face (both faces of the axis must be periodic)
+ *   INFLOW_EQ   the face layer consists of equilibrium cells f = f^eq(rho_b, u_b(z))
+ *               (Sec. 3: equilibrium-based open velocity boundaries)
+ *   OUTFLOW_ZG  zero gradient: a population entering from outside equals the same-direction
+ *               population that left the adjacent in-domain cell (the paper's own outlet is an
+ *               equilibrium face, Sec. 3; zero gradient is this library's open outlet)
+ *   FREESLIP    specular reflection half a spacing outside the face
+ *   NOSLIP      mid-grid bounce-back half a spacing outside the face (App. D)  */
+typedef enum {
+    LBM_FACE_PERIODIC = 0,
+    LBM_FACE_INFLOW_EQ = 1,
+    LBM_FACE_OUTFLOW_ZG = 2,
+    LBM_FACE_FREESLIP = 3,
+    LBM_FACE_NOSLIP = 4
+} lbm_face;
+
+/* Population storage.  Arithmetic is always FP32; populations are stored shifted by their
+ * lattice weight, g_i = f_i - w_i, to keep the stored values small:
+ *   LBM_F32    g as float
+ *   LBM_F16S   g * 2^14 as IEEE binary16, round-to-nearest-even
+ *   LBM_BF16S  g as bfloat16, round-to-nearest-even */
+typedef enum { LBM_F32 = 0, LBM_F16S = 1, LBM_BF16S = 2 } lbm_store;
+
+typedef struct {
+    float tau;            /* molecular relaxation time, > 1/2; nu_0 = (tau - 1/2)/3 (Eq. D.5) */
+    float cs_smag;        /* Smagorinsky constant C (Eq. D.7), >= 0; filter width Delta = 1 */
+    float rho_b;          /* density of the equilibrium boundary cells, > 0 */
+    int store;            /* lbm_store */
+    int face[6];          /* lbm_face, order x- x+ y- y+ z- z+ */
+    float force[3];       /* uniform body-force density, Guo forcing; {0,0,0} = none */
+    int watchdog_every;   /* > 0: lbm_step scans for non-finite populations every that many
+                             steps (synchronises the stream); 0 = off */
+} lbm_params;
+
+/* Fill p with defaults: tau 0.52, C 0.16, rho_b 1, F32, x- inflow, x+ outflow, periodic y,
+ * no-slip ground, free-slip top, no force, no watchdog.  Returns LBM_EINVAL if p is NULL. */
+lbm_status lbm_params_default(lbm_params *p);
+
+/* Lateral face kinds for a wind direction theta (radians, 0 = +x, counter-clockwise): a lateral
+ * face is INFLOW_EQ when the wind enters through it (u . n_in > 1e-6 |u|), OUTFLOW_ZG otherwise;
+ * z- = NOSLIP, z+ = FREESLIP.  face must hold 6 ints. */
+lbm_status lbm_faces_for_direction(float theta, int *face);
+
+/* Bytes of device workspace a domain of this size and storage needs (0 if the arguments are
+ * invalid).  Layout (all regions 256-byte aligned): populations 19 * N * sizeof(store),
+ * cell flags N bytes, inflow profile nz * 3 floats, exit buffers for outflow faces, reduction
+ * scratch. */
+size_t lbm_workspace_bytes(int nx, int ny, int nz, const lbm_params *p);
+
+/* Create a domain in the caller's workspace.
+ *   solid      HOST array of nx*ny*nz bytes, x fastest, nonzero = solid (voxelised buildings,
+ *              Sec. 2.1); copied during the call, may be freed afterwards
+ *   nx,ny,nz   lattice size; >= 2 on every non-periodic axis, >= 1 on periodic ones,
+ *              nx*ny*nz <= 2^31 - 1
+ *   workspace  DEVICE pointer, 256-byte aligned, ws_bytes >= lbm_workspace_bytes()
+ *   stream     cudaStream_t as void* (NULL = default stream); all later calls use it
+ *   out        receives the handle
+ * Cell kinds: solid where the mask is set; otherwise equilibrium cell on an INFLOW_EQ face
+ * layer; otherwise fluid.  The populations start at rest (rho = 1, u = 0) and the inflow profile
+ * at zero; call lbm_set_inflow_profile and lbm_init_fields before stepping. */
+lbm_status lbm_create_domain(const uint8_t *solid, int nx, int ny, int nz, const lbm_params *p,
+                             void *workspace, size_t ws_bytes, void *stream, lbm_domain **out);
+
+/* Replace the stream used by later calls (the caller orders the hand-over). */
+lbm_status lbm_set_stream(lbm_domain *d, void *stream);
+
+/* Set the equilibrium-boundary velocity profile u_b(z) from L level speeds (HOST array) and a
+ * direction theta (radians, 0 = +x, counter-clockwise): u_b = s(z) (cos theta, sin theta, 0).
+ * L divides nz: level l covers the cells z in [l nz/L, (l+1) nz/L).  Otherwise s(z) is linear in
+ * height between level centres (cell z sits at height z + 1/2, level l is centred at
+ * (l + 1/2) nz / L) and constant beyond the outermost centres.  The host array may be reused as
+ * soon as the call returns.  (The paper's per-cell boundary field comes from Kriging of lidar
+ * profiles, Sec. 3 and App. A; this entry point takes the per-height profile directly.) */
+lbm_status lbm_set_inflow_profile(lbm_domain *d, const float *speed, int L, float theta);
+
+/* Initialise the populations to equilibrium, f = f^eq(rho, u) (Eq. D.4), and reset the step
+ * counter to 0.
+ *   rho  DEVICE float[N] or NULL (rho = 1)
+ *   u    DEVICE float[N][3] (u, v, w interleaved per cell) or NULL (u = u_b(z))
+ * Equilibrium cells take f^eq(rho_b, u_b(z)); solid cells are ignored. */
+lbm_status lbm_init_fields(lbm_domain *d, const float *rho, const float *u);
+
+/* Advance n >= 0 time steps (asynchronous).  Each step is one fused kernel over all cells:
+ * gather (Eq. D.3 with the face rules above), moments (D.1), equilibrium (D.4), LES closure
+ * (D.8-D.11), collision (D.2), store.  Streaming is in place on one lattice (odd/even step
+ * pattern), so each step reads and writes every population of every non-solid cell once. */
+lbm_status lbm_step(lbm_domain *d, int n);
+
+/* Number of steps taken since the last lbm_init_fields. */
+long long lbm_steps_done(const lbm_domain *d);
+
+/* Sample (u, v, w, rho) of the current post-collision state at ncol columns and nh heights
+ * (virtual lidar profiles, Sec. 4.4).
+ *   ij   DEVICE int[ncol][2] = (x, y) of each column
+ *   k    DEVICE int[nh] heights (cell z index)
+ *   out  DEVICE float[ncol][nh][4]
+ * Solid cells give (0,0,0,0); equilibrium cells give (u_b(z), rho_b).  An index outside the
+ * lattice gives NaN in all four entries (indices are not checked on the host). */
+lbm_status lbm_sample_columns(lbm_domain *d, const int *ij, int ncol, const int *k, int nh,
+                              float *out);
+
+/* Full macroscopic fields of the current post-collision state (same rules as above).
+ *   rho  DEVICE float[N] (may be NULL);  u  DEVICE float[N][3] (may be NULL) */
+lbm_status lbm_macroscopic(lbm_domain *d, float *rho, float *u);
+
+/* Export the current post-collision populations, shifted, as FP32: g[i * N + c] = f*_i(c) - w_i
+ * in the direction order of lbm_direction_table; solid cells export 0.  DEVICE float[19 * N]. */
+lbm_status lbm_export_populations(lbm_domain *d, float *g);
+
+/* The library's direction order: c[3*i + a] (int) and w[i] (float), i = 0..18.  Returns 19. */
+int lbm_direction_table(int *c, float *w);
+
+/* FP64 reductions over the current state, computed on the GPU and copied to HOST out[4]:
+ *   out[0] = total mass sum rho over fluid cells
+ *   out[1] = net mass flux rho u . n_out summed over the cells of every open (inflow or
+ *            outflow) face layer
+ *   out[2] = max |u| over fluid cells
+ *   out[3] = number of fluid cells with a non-finite population
+ * Synchronises the domain's stream. */
+lbm_status lbm_diagnostics(lbm_domain *d, double *out);
+
+/* Message of the last failed call on this domain ("" if none).  Never NULL. */
+const char *lbm_last_error(const lbm_domain *d);
+
+/* Release the handle (host memory only; the caller frees the workspace).  NULL-safe.  The
+ * caller must make sure no work of this domain is still running if it reuses the workspace. */
+void lbm_destroy(lbm_domain *d);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_B300_H */

@@ -1,0 +1,321 @@
+// lbm_capi.cu -- the C ABI declared in include/lbm.h: argument checks, workspace layout, launches.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+size_t store_bytes(int store) { return store == LBM_F32 ? 4 : 2; }
+
+// Regions of the caller's workspace, in bytes from its start.
+struct Layout {
+    size_t f, flags, ub, side[6], part, diag, total;
+    long long side_cells[6];
+};
+
+bool valid_face(int k) { return k >= LBM_FACE_PERIODIC && k <= LBM_FACE_NOSLIP; }
+
+// Returns nullptr when the arguments are acceptable, else a message.
+const char *check_args(int nx, int ny, int nz, const lbm_params *p) {
+    if (!p) return "params is NULL";
+    if (nx < 1 || ny < 1 || nz < 1) return "lattice dimensions must be >= 1";
+    const long long N = (long long)nx * ny * nz;
+    if (N > INT_MAX) return "nx*ny*nz exceeds 2^31-1 cells";
+    if (!(p->tau > 0.5f) || !std::isfinite(p->tau)) return "tau must be a finite value > 1/2";
+    if (!(p->cs_smag >= 0.0f) || !std::isfinite(p->cs_smag)) return "cs_smag must be finite and >= 0";
+    if (!(p->rho_b > 0.0f) || !std::isfinite(p->rho_b)) return "rho_b must be finite and > 0";
+    if (p->store < LBM_F32 || p->store > LBM_BF16S) return "unknown storage kind";
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(p->force[k])) return "force must be finite";
+    const int n[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) {
+        const int lo = p->face[2 * a], hi = p->face[2 * a + 1];
+        if (!valid_face(lo) || !valid_face(hi)) return "unknown face kind";
+        if ((lo == LBM_FACE_PERIODIC) != (hi == LBM_FACE_PERIODIC))
+            return "a periodic face needs a periodic opposite face";
+        if (lo != LBM_FACE_PERIODIC && n[a] < 2) return "non-periodic axes need at least 2 cells";
+    }
+    if (p->watchdog_every < 0) return "watchdog_every must be >= 0";
+    return nullptr;
+}
+
+Layout make_layout(int nx, int ny, int nz, const lbm_params *p) {
+    Layout L{};
+    const long long N = (long long)nx * ny * nz;
+    const size_t sb = store_bytes(p->store);
+    size_t off = 0;
+    L.f = off; off = align_up(off + (size_t)Q * N * sb);
+    L.flags = off; off = align_up(off + (size_t)N);
+    L.ub = off; off = align_up(off + (size_t)nz * 3 * sizeof(float));
+    const long long fc[3] = {(long long)ny * nz, (long long)nx * nz, (long long)nx * ny};
+    for (int k = 0; k < 6; ++k) {
+        L.side_cells[k] = 0;
+        L.side[k] = 0;
+        if (p->face[k] == LBM_FACE_OUTFLOW_ZG) {
+            L.side_cells[k] = fc[k / 2];
+            L.side[k] = off;
+            off = align_up(off + (size_t)Q * fc[k / 2] * sb);
+        }
+    }
+    L.part = off; off = align_up(off + (size_t)kRedBlocks * 4 * sizeof(double));
+    L.diag = off; off = align_up(off + 4 * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct lbm_domain {
+    int nx, ny, nz;
+    long long N;
+    lbm_params p;
+    cudaStream_t stream;
+    char *ws;
+    Layout L;
+    long long t;                 // steps since init
+    std::vector<float> ub_host;  // expanded profile staging
+    char err[512];
+};
+
+namespace {
+
+lbm_status fail(lbm_domain *d, lbm_status st, const char *fmt, ...) {
+    if (d) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(d->err, sizeof(d->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+lbm_status cuda_check(lbm_domain *d, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return LBM_OK;
+    return fail(d, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+StepArgs args_of(const lbm_domain *d) {
+    StepArgs a{};
+    a.f = d->ws + d->L.f;
+    a.flags = (const uint8_t *)(d->ws + d->L.flags);
+    a.ub = (const float *)(d->ws + d->L.ub);
+    for (int k = 0; k < 6; ++k) a.side[k] = d->L.side_cells[k] ? d->ws + d->L.side[k] : nullptr;
+    a.g.N = d->N;
+    a.g.nx = d->nx; a.g.ny = d->ny; a.g.nz = d->nz;
+    for (int k = 0; k < 6; ++k) a.g.face[k] = d->p.face[k];
+    a.g.sy = d->nx;
+    a.g.sz = (long long)d->nx * d->ny;
+    a.tau = d->p.tau;
+    a.c2x18 = 18.0f * d->p.cs_smag * d->p.cs_smag;
+    a.rho_b = d->p.rho_b;
+    a.fx = d->p.force[0]; a.fy = d->p.force[1]; a.fz = d->p.force[2];
+    return a;
+}
+
+bool has_force(const lbm_domain *d) {
+    return d->p.force[0] != 0.0f || d->p.force[1] != 0.0f || d->p.force[2] != 0.0f;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_params_default(lbm_params *p) {
+    if (!p) return LBM_EINVAL;
+    std::memset(p, 0, sizeof(*p));
+    p->tau = 0.52f;
+    p->cs_smag = 0.16f;
+    p->rho_b = 1.0f;
+    p->store = LBM_F32;
+    const int f[6] = {LBM_FACE_INFLOW_EQ, LBM_FACE_OUTFLOW_ZG, LBM_FACE_PERIODIC,
+                      LBM_FACE_PERIODIC, LBM_FACE_NOSLIP, LBM_FACE_FREESLIP};
+    for (int k = 0; k < 6; ++k) p->face[k] = f[k];
+    return LBM_OK;
+}
+
+lbm_status lbm_faces_for_direction(float theta, int *face) {
+    if (!face || !std::isfinite(theta)) return LBM_EINVAL;
+    const double c = std::cos((double)theta), s = std::sin((double)theta), eps = 1e-6;
+    face[0] = c > eps ? LBM_FACE_INFLOW_EQ : LBM_FACE_OUTFLOW_ZG;
+    face[1] = c < -eps ? LBM_FACE_INFLOW_EQ : LBM_FACE_OUTFLOW_ZG;
+    face[2] = s > eps ? LBM_FACE_INFLOW_EQ : LBM_FACE_OUTFLOW_ZG;
+    face[3] = s < -eps ? LBM_FACE_INFLOW_EQ : LBM_FACE_OUTFLOW_ZG;
+    face[4] = LBM_FACE_NOSLIP;
+    face[5] = LBM_FACE_FREESLIP;
+    return LBM_OK;
+}
+
+size_t lbm_workspace_bytes(int nx, int ny, int nz, const lbm_params *p) {
+    if (check_args(nx, ny, nz, p)) return 0;
+    return make_layout(nx, ny, nz, p).total;
+}
+
+int lbm_direction_table(int *c, float *w) {
+    for (int i = 0; i < Q; ++i) {
+        if (c) { c[3 * i] = cx(i); c[3 * i + 1] = cy(i); c[3 * i + 2] = cz(i); }
+        if (w) w[i] = wgt(i);
+    }
+    return Q;
+}
+
+lbm_status lbm_create_domain(const uint8_t *solid, int nx, int ny, int nz, const lbm_params *p,
+                             void *workspace, size_t ws_bytes, void *stream, lbm_domain **out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    if (!solid || !workspace) return LBM_EINVAL;
+    if (check_args(nx, ny, nz, p)) return LBM_EINVAL;
+    if ((uintptr_t)workspace % kAlign) return LBM_EINVAL;
+    const Layout L = make_layout(nx, ny, nz, p);
+    if (ws_bytes < L.total) return LBM_ENOMEM;
+    lbm_domain *d = new (std::nothrow) lbm_domain();
+    if (!d) return LBM_ENOMEM;
+    d->nx = nx; d->ny = ny; d->nz = nz;
+    d->N = (long long)nx * ny * nz;
+    d->p = *p;
+    d->stream = (cudaStream_t)stream;
+    d->ws = (char *)workspace;
+    d->L = L;
+    d->t = 0;
+    d->err[0] = 0;
+    d->ub_host.assign((size_t)nz * 3, 0.0f);
+
+    StepArgs a = args_of(d);
+    // the population region doubles as staging for the mask (it is initialised right after)
+    uint8_t *mask_dev = (uint8_t *)(d->ws + L.f);
+    lbm_status st = cuda_check(d, cudaMemcpyAsync(mask_dev, solid, (size_t)d->N, cudaMemcpyHostToDevice,
+                                                  d->stream), "mask upload");
+    if (st == LBM_OK) st = cuda_check(d, launch_flags(mask_dev, (uint8_t *)(d->ws + L.flags), a.g, d->stream), "flags kernel");
+    if (st == LBM_OK) st = cuda_check(d, cudaMemsetAsync(d->ws + L.ub, 0, (size_t)nz * 3 * sizeof(float), d->stream), "profile clear");
+    for (int k = 0; k < 6 && st == LBM_OK; ++k)
+        if (L.side_cells[k])
+            st = cuda_check(d, cudaMemsetAsync(d->ws + L.side[k], 0, (size_t)Q * L.side_cells[k] * store_bytes(p->store), d->stream), "side buffer clear");
+    if (st == LBM_OK) st = cuda_check(d, launch_init(p->store, a, nullptr, nullptr, d->stream), "init kernel");
+    if (st != LBM_OK) {
+        delete d;
+        return st;
+    }
+    *out = d;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_stream(lbm_domain *d, void *stream) {
+    if (!d) return LBM_EINVAL;
+    d->stream = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_inflow_profile(lbm_domain *d, const float *speed, int L, float theta) {
+    if (!d) return LBM_EINVAL;
+    if (!speed || L < 1) return fail(d, LBM_EINVAL, "set_inflow_profile: need L >= 1 speeds");
+    if (!std::isfinite(theta)) return fail(d, LBM_EINVAL, "set_inflow_profile: theta not finite");
+    for (int l = 0; l < L; ++l)
+        if (!std::isfinite(speed[l])) return fail(d, LBM_EINVAL, "set_inflow_profile: speed[%d] not finite", l);
+    const int nz = d->nz;
+    const double c = std::cos((double)theta), s = std::sin((double)theta);
+    for (int k = 0; k < nz; ++k) {
+        double v;
+        if (nz % L == 0) {
+            v = speed[k / (nz / L)];
+        } else {
+            const double pos = (k + 0.5) * L / nz - 0.5;   // in units of level centres
+            if (pos <= 0.0) v = speed[0];
+            else if (pos >= L - 1) v = speed[L - 1];
+            else {
+                const int l = (int)pos;
+                const double w = pos - l;
+                v = (1.0 - w) * speed[l] + w * speed[l + 1];
+            }
+        }
+        d->ub_host[3 * k] = (float)(v * c);
+        d->ub_host[3 * k + 1] = (float)(v * s);
+        d->ub_host[3 * k + 2] = 0.0f;
+    }
+    return cuda_check(d, cudaMemcpyAsync(d->ws + d->L.ub, d->ub_host.data(), (size_t)nz * 3 * sizeof(float),
+                                         cudaMemcpyHostToDevice, d->stream), "profile upload");
+}
+
+lbm_status lbm_init_fields(lbm_domain *d, const float *rho, const float *u) {
+    if (!d) return LBM_EINVAL;
+    const StepArgs a = args_of(d);
+    lbm_status st = cuda_check(d, launch_init(d->p.store, a, rho, u, d->stream), "init kernel");
+    if (st == LBM_OK) d->t = 0;
+    return st;
+}
+
+lbm_status lbm_diagnostics(lbm_domain *d, double *out) {
+    if (!d || !out) return LBM_EINVAL;
+    const StepArgs a = args_of(d);
+    double *part = (double *)(d->ws + d->L.part);
+    double *res = (double *)(d->ws + d->L.diag);
+    lbm_status st = cuda_check(d, launch_reduce(d->p.store, a, (d->t & 1) != 0, part, res, d->stream), "reduce kernels");
+    if (st != LBM_OK) return st;
+    st = cuda_check(d, cudaMemcpyAsync(out, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, d->stream), "diagnostics copy");
+    if (st != LBM_OK) return st;
+    return cuda_check(d, cudaStreamSynchronize(d->stream), "diagnostics sync");
+}
+
+lbm_status lbm_step(lbm_domain *d, int n) {
+    if (!d) return LBM_EINVAL;
+    if (n < 0) return fail(d, LBM_EINVAL, "step: n must be >= 0");
+    const StepArgs a = args_of(d);
+    const bool force = has_force(d);
+    for (int k = 0; k < n; ++k) {
+        launch_step(d->p.store, (d->t & 1) == 0, force, a, d->stream);
+        d->t += 1;
+        if (d->p.watchdog_every > 0 && d->t % d->p.watchdog_every == 0) {
+            double diag[4];
+            lbm_status st = lbm_diagnostics(d, diag);
+            if (st != LBM_OK) return st;
+            if (diag[3] > 0.0)
+                return fail(d, LBM_EUNSTABLE, "watchdog: %.0f fluid cells with non-finite populations at step %lld",
+                            diag[3], d->t);
+        }
+    }
+    return cuda_check(d, cudaGetLastError(), "step kernel launch");
+}
+
+long long lbm_steps_done(const lbm_domain *d) { return d ? d->t : -1; }
+
+lbm_status lbm_sample_columns(lbm_domain *d, const int *ij, int ncol, const int *k, int nh, float *out) {
+    if (!d) return LBM_EINVAL;
+    if (ncol < 0 || nh < 0) return fail(d, LBM_EINVAL, "sample: negative counts");
+    if ((long long)ncol * nh == 0) return LBM_OK;
+    if (!ij || !k || !out) return fail(d, LBM_EINVAL, "sample: NULL pointer");
+    const StepArgs a = args_of(d);
+    return cuda_check(d, launch_sample(d->p.store, a, (d->t & 1) != 0, ij, ncol, k, nh, out, d->stream), "sample kernel");
+}
+
+lbm_status lbm_macroscopic(lbm_domain *d, float *rho, float *u) {
+    if (!d) return LBM_EINVAL;
+    if (!rho && !u) return LBM_OK;
+    const StepArgs a = args_of(d);
+    return cuda_check(d, launch_macros(d->p.store, a, (d->t & 1) != 0, rho, u, d->stream), "macroscopic kernel");
+}
+
+lbm_status lbm_export_populations(lbm_domain *d, float *g) {
+    if (!d) return LBM_EINVAL;
+    if (!g) return fail(d, LBM_EINVAL, "export: NULL pointer");
+    const StepArgs a = args_of(d);
+    return cuda_check(d, launch_export(d->p.store, a, (d->t & 1) != 0, g, d->stream), "export kernel");
+}
+
+const char *lbm_last_error(const lbm_domain *d) { return d ? d->err : "no domain"; }
+
+void lbm_destroy(lbm_domain *d) { delete d; }
+
+}  // extern "C"

@@ -1,0 +1,23 @@
+// lbm_internal.h -- launchers shared by the kernels (lbm_kernels.cu) and the C ABI (lbm_capi.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+constexpr int kRedBlocks = 148 * 8;   // diagnostics pass-1 blocks (8 per SM on a 148-SM B300)
+
+cudaError_t launch_flags(const uint8_t *mask, uint8_t *flags, const Geo &G, cudaStream_t s);
+cudaError_t launch_init(int store, const StepArgs &a, const float *rho, const float *u, cudaStream_t s);
+void launch_step(int store, bool neighbor, bool force, const StepArgs &a, cudaStream_t s);
+cudaError_t launch_macros(int store, const StepArgs &a, bool layoutA, float *rho, float *u,
+                          cudaStream_t s);
+cudaError_t launch_sample(int store, const StepArgs &a, bool layoutA, const int *ij, int ncol,
+                          const int *k, int nh, float *out, cudaStream_t s);
+cudaError_t launch_export(int store, const StepArgs &a, bool layoutA, float *out, cudaStream_t s);
+cudaError_t launch_reduce(int store, const StepArgs &a, bool layoutA, double *part, double *out,
+                          cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,262 @@
+// lbm_kernels.cu -- sm_103a kernels of the LBM-LES step and their launchers.
+//
+// Hot path: k_step_neighbor (layout B -> A) and k_step_local (layout A -> B), one launch per
+// time step, one thread per cell, populations as 19 structure-of-arrays planes with x fastest.
+// Both are HBM-bound stencils (about 2 flop per byte): no tensor cores, no shared-memory staging;
+// every warp reads and writes 32 consecutive cells of each plane (fully coalesced; the neighbour
+// step's x-shifted planes straddle one extra 32-byte sector that the next warp uses).
+#include <cuda_runtime.h>
+
+#include "lbm_cell.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+constexpr int kBlock = 256;
+
+// ---------------------------------------------------------------- grid wrappers
+#define LBM_CELL_INDEX()                                                   \
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; \
+    if (n >= G_N) return;
+
+__global__ void k_flags(const uint8_t *__restrict__ mask, uint8_t *__restrict__ flags, Geo G) {
+    const long long G_N = G.N;
+    LBM_CELL_INDEX();
+    cell_flags(mask, flags, G, n);
+}
+
+template <int S>
+__global__ void k_init(StepArgs a, const float *__restrict__ rho, const float *__restrict__ u) {
+    const long long G_N = a.g.N;
+    LBM_CELL_INDEX();
+    cell_init<S>(a, n, rho, u);
+}
+
+template <int S, bool FORCE>
+__global__ void __launch_bounds__(kBlock) k_step_local(StepArgs a) {
+    const long long G_N = a.g.N;
+    LBM_CELL_INDEX();
+    cell_local<S, FORCE>(a, n);
+}
+
+template <int S, bool FORCE>
+__global__ void __launch_bounds__(kBlock) k_step_neighbor(StepArgs a) {
+    const long long G_N = a.g.N;
+    LBM_CELL_INDEX();
+    cell_neighbor<S, FORCE>(a, n);
+}
+
+template <int S>
+__global__ void k_macros(StepArgs a, bool layoutA, float *__restrict__ rho_out,
+                         float *__restrict__ u_out) {
+    const long long G_N = a.g.N;
+    LBM_CELL_INDEX();
+    float r, ux, uy, uz;
+    cell_macros<S>(a, n, layoutA, r, ux, uy, uz);
+    if (rho_out) rho_out[n] = r;
+    if (u_out) { u_out[3 * n] = ux; u_out[3 * n + 1] = uy; u_out[3 * n + 2] = uz; }
+}
+
+template <int S>
+__global__ void k_sample(StepArgs a, bool layoutA, const int *__restrict__ ij, int ncol,
+                         const int *__restrict__ kk, int nh, float *__restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)ncol * nh) return;
+    const int c = (int)(t / nh), h = (int)(t - (long long)c * nh);
+    const int x = ij[2 * c], y = ij[2 * c + 1], z = kk[h];
+    float *o = out + 4 * t;
+    if (x < 0 || x >= a.g.nx || y < 0 || y >= a.g.ny || z < 0 || z >= a.g.nz) {
+        o[0] = o[1] = o[2] = o[3] = NAN;
+        return;
+    }
+    float r, ux, uy, uz;
+    cell_macros<S>(a, cell_of(a.g, x, y, z), layoutA, r, ux, uy, uz);
+    o[0] = ux; o[1] = uy; o[2] = uz; o[3] = r;
+}
+
+template <int S>
+__global__ void k_export(StepArgs a, bool layoutA, float *__restrict__ out) {
+    const long long G_N = a.g.N;
+    LBM_CELL_INDEX();
+    cell_export<S>(a, n, layoutA, out);
+}
+
+// ---------------------------------------------------------------- FP64 diagnostics
+// Pass 1: kRedBlocks blocks stride over the lattice; each writes 4 partials into scratch.
+// Pass 2: one block folds the partials.  Fixed block count -> deterministic result.
+template <int S>
+__global__ void __launch_bounds__(kBlock) k_reduce_partial(StepArgs a, bool layoutA,
+                                                           double *__restrict__ part) {
+    double mass = 0.0, flux = 0.0, umax = 0.0, bad = 0.0;
+    const long long stride = (long long)gridDim.x * kBlock;
+    for (long long n = (long long)blockIdx.x * kBlock + threadIdx.x; n < a.g.N; n += stride) {
+        const uint8_t fl = a.flags[n];
+        if (fl & F_SOLID) continue;
+        float r, ux, uy, uz;
+        int x, y, z;
+        cell_coords(a.g, n, x, y, z);
+        if (fl & F_EQ) {
+            r = a.rho_b; ux = a.ub[3 * z]; uy = a.ub[3 * z + 1]; uz = a.ub[3 * z + 2];
+        } else {
+            float g[Q];
+            read_post<S>(a, n, fl, layoutA, g);
+            bool finite = true;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) finite &= isfinite(g[i]);
+            if (!finite) { bad += 1.0; continue; }
+            macros_of(a, g, r, ux, uy, uz);
+            mass += (double)r;
+            const double um = sqrt((double)ux * ux + (double)uy * uy + (double)uz * uz);
+            umax = um > umax ? um : umax;
+        }
+        // outward mass flux through every open face layer the cell lies on
+        const float uu[3] = {ux, uy, uz};
+        const int p[3] = {x, y, z};
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const int fl0 = a.g.face[2 * ax], fl1 = a.g.face[2 * ax + 1];
+            const bool open0 = fl0 == LBM_FACE_INFLOW_EQ || fl0 == LBM_FACE_OUTFLOW_ZG;
+            const bool open1 = fl1 == LBM_FACE_INFLOW_EQ || fl1 == LBM_FACE_OUTFLOW_ZG;
+            if (open0 && p[ax] == 0) flux -= (double)r * uu[ax];
+            if (open1 && p[ax] == dim(a.g, ax) - 1) flux += (double)r * uu[ax];
+        }
+    }
+    __shared__ double sh[4][kBlock];
+    sh[0][threadIdx.x] = mass; sh[1][threadIdx.x] = flux;
+    sh[2][threadIdx.x] = umax; sh[3][threadIdx.x] = bad;
+    __syncthreads();
+    for (int s = kBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
+            sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + s]);
+            sh[3][threadIdx.x] += sh[3][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) part[4 * blockIdx.x + k] = sh[k][0];
+}
+
+__global__ void __launch_bounds__(kBlock) k_reduce_final(const double *__restrict__ part, int nb,
+                                                         double *__restrict__ out) {
+    __shared__ double sh[4][kBlock];
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nb; b += kBlock) {
+        v[0] += part[4 * b];
+        v[1] += part[4 * b + 1];
+        v[2] = fmax(v[2], part[4 * b + 2]);
+        v[3] += part[4 * b + 3];
+    }
+    for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int s = kBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
+            sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + s]);
+            sh[3][threadIdx.x] += sh[3][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) out[k] = sh[k][0];
+}
+
+// ---------------------------------------------------------------- launchers
+static inline unsigned blocks_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+cudaError_t launch_flags(const uint8_t *mask, uint8_t *flags, const Geo &G, cudaStream_t s) {
+    k_flags<<<blocks_for(G.N), kBlock, 0, s>>>(mask, flags, G);
+    return cudaGetLastError();
+}
+
+template <int S>
+static cudaError_t init_t(const StepArgs &a, const float *rho, const float *u, cudaStream_t s) {
+    k_init<S><<<blocks_for(a.g.N), kBlock, 0, s>>>(a, rho, u);
+    return cudaGetLastError();
+}
+cudaError_t launch_init(int store, const StepArgs &a, const float *rho, const float *u, cudaStream_t s) {
+    switch (store) {
+        case LBM_F32: return init_t<LBM_F32>(a, rho, u, s);
+        case LBM_F16S: return init_t<LBM_F16S>(a, rho, u, s);
+        default: return init_t<LBM_BF16S>(a, rho, u, s);
+    }
+}
+
+template <int S, bool FORCE>
+static void step_t(bool neighbor, const StepArgs &a, cudaStream_t s) {
+    if (neighbor) k_step_neighbor<S, FORCE><<<blocks_for(a.g.N), kBlock, 0, s>>>(a);
+    else k_step_local<S, FORCE><<<blocks_for(a.g.N), kBlock, 0, s>>>(a);
+}
+template <int S>
+static void step_s(bool neighbor, bool force, const StepArgs &a, cudaStream_t s) {
+    if (force) step_t<S, true>(neighbor, a, s);
+    else step_t<S, false>(neighbor, a, s);
+}
+void launch_step(int store, bool neighbor, bool force, const StepArgs &a, cudaStream_t s) {
+    switch (store) {
+        case LBM_F32: step_s<LBM_F32>(neighbor, force, a, s); break;
+        case LBM_F16S: step_s<LBM_F16S>(neighbor, force, a, s); break;
+        default: step_s<LBM_BF16S>(neighbor, force, a, s); break;
+    }
+}
+
+template <int S>
+static cudaError_t macros_t(const StepArgs &a, bool layoutA, float *rho, float *u, cudaStream_t s) {
+    k_macros<S><<<blocks_for(a.g.N), kBlock, 0, s>>>(a, layoutA, rho, u);
+    return cudaGetLastError();
+}
+cudaError_t launch_macros(int store, const StepArgs &a, bool layoutA, float *rho, float *u,
+                          cudaStream_t s) {
+    switch (store) {
+        case LBM_F32: return macros_t<LBM_F32>(a, layoutA, rho, u, s);
+        case LBM_F16S: return macros_t<LBM_F16S>(a, layoutA, rho, u, s);
+        default: return macros_t<LBM_BF16S>(a, layoutA, rho, u, s);
+    }
+}
+
+template <int S>
+static cudaError_t sample_t(const StepArgs &a, bool layoutA, const int *ij, int ncol, const int *k,
+                            int nh, float *out, cudaStream_t s) {
+    k_sample<S><<<blocks_for((long long)ncol * nh), kBlock, 0, s>>>(a, layoutA, ij, ncol, k, nh, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_sample(int store, const StepArgs &a, bool layoutA, const int *ij, int ncol,
+                          const int *k, int nh, float *out, cudaStream_t s) {
+    switch (store) {
+        case LBM_F32: return sample_t<LBM_F32>(a, layoutA, ij, ncol, k, nh, out, s);
+        case LBM_F16S: return sample_t<LBM_F16S>(a, layoutA, ij, ncol, k, nh, out, s);
+        default: return sample_t<LBM_BF16S>(a, layoutA, ij, ncol, k, nh, out, s);
+    }
+}
+
+template <int S>
+static cudaError_t export_t(const StepArgs &a, bool layoutA, float *out, cudaStream_t s) {
+    k_export<S><<<blocks_for(a.g.N), kBlock, 0, s>>>(a, layoutA, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_export(int store, const StepArgs &a, bool layoutA, float *out, cudaStream_t s) {
+    switch (store) {
+        case LBM_F32: return export_t<LBM_F32>(a, layoutA, out, s);
+        case LBM_F16S: return export_t<LBM_F16S>(a, layoutA, out, s);
+        default: return export_t<LBM_BF16S>(a, layoutA, out, s);
+    }
+}
+
+template <int S>
+static cudaError_t reduce_t(const StepArgs &a, bool layoutA, double *part, double *out, cudaStream_t s) {
+    k_reduce_partial<S><<<kRedBlocks, kBlock, 0, s>>>(a, layoutA, part);
+    k_reduce_final<<<1, kBlock, 0, s>>>(part, kRedBlocks, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_reduce(int store, const StepArgs &a, bool layoutA, double *part, double *out,
+                          cudaStream_t s) {
+    switch (store) {
+        case LBM_F32: return reduce_t<LBM_F32>(a, layoutA, part, out, s);
+        case LBM_F16S: return reduce_t<LBM_F16S>(a, layoutA, part, out, s);
+        default: return reduce_t<LBM_BF16S>(a, layoutA, part, out, s);
+    }
+}
+
+}  // namespace lbm

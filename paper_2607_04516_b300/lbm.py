@@ -1,0 +1,260 @@
+"""Thin Python binding of the C ABI in ``include/lbm.h`` (argument marshalling only).
+
+Every entry point keeps its C name (``lbm_create_domain``, ``lbm_step``, ...) and forwards torch
+CUDA tensors as raw device pointers; all computation happens in ``liblbm.so``.  The library is
+loaded on first use; a missing library or a missing CUDA device raises ``RuntimeError`` -- there
+is no fallback path.  ``Domain`` bundles the calls for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbm.so")
+
+FACES = {"periodic": 0, "inflow": 1, "outflow": 2, "freeslip": 3, "noslip": 4}
+FACE_NAMES = {v: k for k, v in FACES.items()}
+STORES = {"f32": 0, "f16s": 1, "bf16s": 2}
+STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_EUNSTABLE",
+          -5: "LBM_ESTATE"}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_float), ("cs_smag", ctypes.c_float), ("rho_b", ctypes.c_float),
+                ("store", ctypes.c_int), ("face", ctypes.c_int * 6), ("force", ctypes.c_float * 3),
+                ("watchdog_every", ctypes.c_int)]
+
+
+# exported symbols and their ctypes signatures (the header is the authority)
+_P, _I, _F, _LL, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_longlong, ctypes.c_size_t
+_PP = ctypes.POINTER(lbm_params)
+SIGNATURES = {
+    "lbm_params_default": (_I, [_PP]),
+    "lbm_faces_for_direction": (_I, [_F, _P]),
+    "lbm_workspace_bytes": (_SZ, [_I, _I, _I, _PP]),
+    "lbm_create_domain": (_I, [_P, _I, _I, _I, _PP, _P, _SZ, _P, ctypes.POINTER(_P)]),
+    "lbm_set_stream": (_I, [_P, _P]),
+    "lbm_set_inflow_profile": (_I, [_P, _P, _I, _F]),
+    "lbm_init_fields": (_I, [_P, _P, _P]),
+    "lbm_step": (_I, [_P, _I]),
+    "lbm_steps_done": (_LL, [_P]),
+    "lbm_sample_columns": (_I, [_P, _P, _I, _P, _I, _P]),
+    "lbm_macroscopic": (_I, [_P, _P, _P]),
+    "lbm_export_populations": (_I, [_P, _P]),
+    "lbm_direction_table": (_I, [_P, _P]),
+    "lbm_diagnostics": (_I, [_P, _P]),
+    "lbm_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+def load(require_gpu: bool = True) -> ctypes.CDLL:
+    """Load ``liblbm.so`` (raises if it is missing; with ``require_gpu`` also without a GPU)."""
+    global _lib
+    if require_gpu:
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblbm needs a CUDA device; none is visible")
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} not built: run `python -m paper_2607_04516_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    import torch
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _check(status: int, dom=None):
+    if status != 0:
+        msg = load(False).lbm_last_error(dom).decode() if dom else ""
+        raise LbmError(status, msg)
+
+
+def make_params(faces, tau=0.52, cs=0.16, store="f32", rho_b=1.0, force=None, watchdog_every=0):
+    p = lbm_params()
+    load(False).lbm_params_default(ctypes.byref(p))
+    p.tau = tau
+    p.cs_smag = cs
+    p.rho_b = rho_b
+    p.store = STORES[store] if isinstance(store, str) else int(store)
+    for k, f in enumerate(faces):
+        p.face[k] = FACES[f] if isinstance(f, str) else int(f)
+    for k in range(3):
+        p.force[k] = 0.0 if force is None else float(force[k])
+    p.watchdog_every = watchdog_every
+    return p
+
+
+# ------------------------------------------------------------------ C-named entry points
+def lbm_faces_for_direction(theta: float) -> tuple:
+    face = (ctypes.c_int * 6)()
+    _check(load(False).lbm_faces_for_direction(theta, face))
+    return tuple(FACE_NAMES[v] for v in face)
+
+
+def lbm_workspace_bytes(nx: int, ny: int, nz: int, params: lbm_params) -> int:
+    return load(False).lbm_workspace_bytes(nx, ny, nz, ctypes.byref(params))
+
+
+def lbm_direction_table():
+    c = np.zeros(57, np.int32)
+    w = np.zeros(19, np.float32)
+    load(False).lbm_direction_table(c.ctypes.data, w.ctypes.data)
+    return c.reshape(19, 3).astype(np.int64), w
+
+
+def lbm_create_domain(solid: np.ndarray, params: lbm_params, workspace, stream: int | None):
+    solid = np.ascontiguousarray(solid, np.uint8)
+    nz, ny, nx = solid.shape
+    out = _P()
+    st = load().lbm_create_domain(solid.ctypes.data, nx, ny, nz, ctypes.byref(params),
+                                  workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                  stream, ctypes.byref(out))
+    _check(st)
+    return out
+
+
+def lbm_set_inflow_profile(dom, speed, theta: float):
+    sp = np.ascontiguousarray(speed, np.float32) if not hasattr(speed, "data_ptr") else speed
+    _check(load().lbm_set_inflow_profile(dom, _ptr(sp), len(sp), float(theta)), dom)
+
+
+def lbm_init_fields(dom, rho=None, u=None):
+    _check(load().lbm_init_fields(dom, _ptr(rho), _ptr(u)), dom)
+
+
+def lbm_step(dom, n: int):
+    _check(load().lbm_step(dom, int(n)), dom)
+
+
+def lbm_steps_done(dom) -> int:
+    return load().lbm_steps_done(dom)
+
+
+def lbm_sample_columns(dom, ij, k, out):
+    _check(load().lbm_sample_columns(dom, _ptr(ij), ij.shape[0], _ptr(k), k.shape[0], _ptr(out)), dom)
+
+
+def lbm_macroscopic(dom, rho=None, u=None):
+    _check(load().lbm_macroscopic(dom, _ptr(rho), _ptr(u)), dom)
+
+
+def lbm_export_populations(dom, g):
+    _check(load().lbm_export_populations(dom, _ptr(g)), dom)
+
+
+def lbm_diagnostics(dom) -> dict:
+    out = np.zeros(4, np.float64)
+    _check(load().lbm_diagnostics(dom, out.ctypes.data), dom)
+    return {"mass": out[0], "net_flux": out[1], "umax": out[2], "nonfinite": int(out[3])}
+
+
+def lbm_destroy(dom):
+    load(False).lbm_destroy(dom)
+
+
+# ------------------------------------------------------------------ convenience wrapper
+class Domain:
+    """One lattice in a torch-owned workspace on the current CUDA device and stream."""
+
+    def __init__(self, solid: np.ndarray, faces, tau: float = 0.52, cs: float = 0.16,
+                 store: str = "f32", rho_b: float = 1.0, force=None, watchdog_every: int = 0,
+                 device: str = "cuda", stream=None):
+        import torch
+        load()
+        self.shape = tuple(solid.shape)
+        nz, ny, nx = self.shape
+        self.N = nx * ny * nz
+        self.faces = tuple(faces)
+        self.store = store
+        self.params = make_params(faces, tau, cs, store, rho_b, force, watchdog_every)
+        nbytes = lbm_workspace_bytes(nx, ny, nz, self.params)
+        if nbytes == 0:
+            raise LbmError(-1, "invalid domain arguments")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.workspace.device)
+        self.dom = lbm_create_domain(solid, self.params, self.workspace, self.stream.cuda_stream)
+
+    # the handle is released with the object; the workspace tensor is freed by torch
+    def __del__(self):
+        dom = getattr(self, "dom", None)
+        if dom:
+            lbm_destroy(dom)
+            self.dom = None
+
+    @property
+    def device(self):
+        return self.workspace.device
+
+    def set_inflow_profile(self, speed, theta: float = 0.0):
+        lbm_set_inflow_profile(self.dom, speed, theta)
+
+    def init_fields(self, rho=None, u=None):
+        import torch
+        r = None if rho is None else torch.as_tensor(rho, dtype=torch.float32, device=self.device).contiguous()
+        v = None if u is None else torch.as_tensor(u, dtype=torch.float32, device=self.device).contiguous()
+        lbm_init_fields(self.dom, r, v)
+        self._keep = (r, v)   # keep alive until the stream has consumed them
+
+    def step(self, n: int = 1):
+        lbm_step(self.dom, n)
+
+    @property
+    def steps_done(self) -> int:
+        return lbm_steps_done(self.dom)
+
+    def macroscopic(self):
+        import torch
+        nz, ny, nx = self.shape
+        rho = torch.empty((nz, ny, nx), dtype=torch.float32, device=self.device)
+        u = torch.empty((nz, ny, nx, 3), dtype=torch.float32, device=self.device)
+        lbm_macroscopic(self.dom, rho, u)
+        return rho, u
+
+    def export_populations(self):
+        import torch
+        g = torch.empty((19,) + self.shape, dtype=torch.float32, device=self.device)
+        lbm_export_populations(self.dom, g)
+        return g
+
+    def sample_columns(self, ij, k, out=None):
+        import torch
+        ij = torch.as_tensor(ij, dtype=torch.int32, device=self.device).contiguous()
+        k = torch.as_tensor(k, dtype=torch.int32, device=self.device).contiguous()
+        if out is None:
+            out = torch.empty((ij.shape[0], k.shape[0], 4), dtype=torch.float32, device=self.device)
+        lbm_sample_columns(self.dom, ij, k, out)
+        return out
+
+    def diagnostics(self) -> dict:
+        return lbm_diagnostics(self.dom)
+
+
+def glups(cells: int, steps: int, seconds: float) -> float:
+    return cells * steps / seconds / 1e9 if seconds > 0 else math.nan

@@ -68,9 +68,10 @@ def direction_from_seed(seed: int) -> float:
 
 def faces_for_direction(theta: float, bottom: str = "noslip", top: str = "freeslip") -> tuple:
     """A lateral face is an inflow face when the wind blows into the domain through it
-    (u . n_in > 0), an outflow face otherwise."""
+    (u . n_in > 0), an outflow face otherwise; a wind within 1e-6 of parallel to a face counts as
+    parallel (outflow on both sides)."""
     cx, cy = math.cos(theta), math.sin(theta)
-    eps = 1e-12
+    eps = 1e-6
     return ("inflow" if cx > eps else "outflow", "inflow" if cx < -eps else "outflow",
             "inflow" if cy > eps else "outflow", "inflow" if cy < -eps else "outflow",
             bottom, top)

@@ -1,0 +1,96 @@
+"""Shared helpers of the GPU parity tests: run a case through the C ABI and through the oracle on
+the same seeded inputs (inputs rounded to FP32 once, so both sides start from identical values)."""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import oracle as orc
+from paper_2607_04516_b300 import synth
+
+TOL_U = {"f32": 1e-5, "f16s": 1e-3, "bf16s": 1e-2}   # relative L2 of u over fluid cells
+
+
+def f32(a):
+    return None if a is None else np.asarray(a, np.float32)
+
+
+def f64_of_f32(a):
+    return None if a is None else np.asarray(a, np.float32).astype(np.float64)
+
+
+def lib_to_oracle_order():
+    """Index list p with oracle_array = lib_array[p]."""
+    from paper_2607_04516_b300 import lbm
+    c_lib, _ = lbm.lbm_direction_table()
+    c_or, _, _ = orc.lattice()
+    return [int(np.nonzero((c_lib == c_or[i]).all(1))[0][0]) for i in range(19)]
+
+
+def gpu_domain(case: synth.Case, store: str = "f32", **kw):
+    from paper_2607_04516_b300 import lbm
+    dom = lbm.Domain(case.solid, case.faces, case.tau, case.cs, store, case.rho_b, case.force, **kw)
+    dom.set_inflow_profile(f32(case.speed), case.theta)
+    dom.init_fields(f32(case.rho0), f32(case.u0))
+    return dom
+
+
+def gpu_run(case: synth.Case, nsteps: int, store: str = "f32"):
+    import torch
+    dom = gpu_domain(case, store)
+    dom.step(nsteps)
+    rho, u = dom.macroscopic()
+    torch.cuda.synchronize()
+    return rho.cpu().numpy().astype(np.float64), u.cpu().numpy().astype(np.float64), dom
+
+
+def oracle_inputs(case: synth.Case):
+    nz = case.shape[0]
+    kind = orc.classify(case.solid, case.faces)
+    # the library expands float32 level speeds; give the oracle the same numbers
+    ub = orc.expand_profile(f64_of_f32(case.speed), nz, float(np.float32(case.theta)))
+    return kind, ub
+
+
+def oracle_run(case: synth.Case, nsteps: int):
+    kind, ub = oracle_inputs(case)
+    F = orc.init(kind, ub, f64_of_f32(case.rho0), f64_of_f32(case.u0), case.rho_b)
+    F = orc.run(F, nsteps, kind, case.faces, ub, case.tau, case.cs, force=case.force,
+                rho_b=case.rho_b)
+    rho, u = orc.macros(F, kind, ub, case.rho_b, case.force)
+    return rho, u, F, kind, ub
+
+
+def rel_l2(a, b, mask):
+    return float(np.linalg.norm((a - b)[mask]) / np.linalg.norm(b[mask]))
+
+
+def oracle_one_step_planes(g_lib: np.ndarray, kind: np.ndarray, faces, ub: np.ndarray, tau: float,
+                           cs: float, force, rho_b: float, planes, perm):
+    """Oracle step from a given post-collision state (library-order shifted FP32 populations of
+    planes z-1..z+1 for every requested z) to the next one, on the requested planes only.
+    Returns {z: F_next plane (19, ny, nx) in oracle order}.  Gathers of plane z reach z +- 1 only,
+    so a three-plane slab (with the true z face where it touches the lattice boundary) is exact."""
+    _, wo, _ = orc.lattice()
+    nz = kind.shape[0]
+    out = {}
+    for z in planes:
+        za, zb = max(z - 1, 0), min(z + 1, nz - 1)
+        sl = slice(za, zb + 1)
+        G = g_lib[:, sl].astype(np.float64)[perm]            # oracle order
+        F = G + wo[:, None, None, None]
+        kk = np.ascontiguousarray(kind[sl])
+        F[:, kk == orc.SOLID] = 0.0
+        fz = list(faces)
+        if za > 0:
+            fz[4] = "outflow"      # artificial slab face, never reached by plane z's gathers
+        if zb < nz - 1:
+            fz[5] = "outflow"
+        if faces[4] == "periodic" and (za > 0 or zb < nz - 1):
+            fz[4] = fz[5] = "outflow"
+        # re-classify: equilibrium layers of artificial faces must not appear
+        kk2 = orc.classify((kk == orc.SOLID).astype(np.uint8), fz)
+        assert (kk2 == kk).all()
+        Fn = orc.step(np.ascontiguousarray(F), kk, fz, np.ascontiguousarray(ub[sl]), tau, cs,
+                      force=force, rho_b=rho_b, z0=z - za, z1=z - za + 1)
+        out[z] = Fn[:, z - za]
+    return out
