@@ -124,6 +124,7 @@ StepArgs args_of(const lbm_domain *d) {
     a.c2x18 = 18.0f * d->p.cs_smag * d->p.cs_smag;
     a.rho_b = d->p.rho_b;
     a.fx = d->p.force[0]; a.fy = d->p.force[1]; a.fz = d->p.force[2];
+    a.nface = face_cell_count(a.g);
     return a;
 }
 

@@ -26,15 +26,14 @@ LBM_HD void cell_flags(const uint8_t *__restrict__ mask, uint8_t *__restrict__ f
     for (int a = 0; a < 3; ++a)
         zgl |= (lo[a] && G.face[2 * a] == LBM_FACE_OUTFLOW_ZG) || (hi[a] && G.face[2 * a + 1] == LBM_FACE_OUTFLOW_ZG);
     uint8_t fl = zgl ? F_ZG : 0;
+    if (onface) fl |= F_FACE;
     if (eq) {
-        fl |= F_EQ | F_SLOW;
-    } else {
-        bool slow = onface;
-        if (!slow) {   // interior cell: all 18 neighbours are in range
+        fl |= F_EQ;
+    } else if (!onface) {   // interior cell: all 18 neighbours are in range
+        bool near = false;
 #pragma unroll
-            for (int i = 1; i < Q; ++i) slow |= mask[n + cx(i) + cy(i) * G.sy + cz(i) * G.sz] != 0;
-        }
-        if (slow) fl |= F_SLOW;
+        for (int i = 1; i < Q; ++i) near |= mask[n + cx(i) + cy(i) * G.sy + cz(i) * G.sz] != 0;
+        if (near) fl |= F_NEAR;
     }
     flags[n] = fl;
 }
@@ -102,33 +101,46 @@ LBM_HD void cell_local(const StepArgs &a, long long n) {
 }
 
 // ---------------------------------------------------------------- neighbour step: B -> A
+// Interior cell (on no face layer): pull from x - c_i and push to x + c_i; a solid neighbour turns
+// the link into bounce-back (read / write the cell's own reversed slot).  The 18 neighbour flags
+// are loaded only for cells marked F_NEAR.
 template <int S, bool FORCE>
-LBM_HD void cell_neighbor(const StepArgs &a, long long n) {
+LBM_HD void cell_neighbor_interior(const StepArgs &a, long long n, uint8_t fl) {
     using Cd = Codec<S>;
     using T = typename Cd::T;
-    const uint8_t fl = a.flags[n];
-    if (fl & F_SOLID) return;
     T *__restrict__ f = (T *)a.f;
     const long long N = a.g.N;
     const long long sy = a.g.sy, sz = a.g.sz;
-    float g[Q];
-    if (!(fl & F_SLOW)) {
-        // interior fluid cell without solid neighbours: plain pull, plain push
+    unsigned nb = 0;   // bit i: the neighbour x + c_i is solid
+    if (fl & F_NEAR) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const long long off = cx(i) + cy(i) * sy + cz(i) * sz;
-            g[i] = Cd::dec(f[(long long)opp(i) * N + n - off]);
-        }
-        collide<FORCE>(g, a);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const long long off = cx(i) + cy(i) * sy + cz(i) * sz;
-            f[(long long)i * N + n + off] = Cd::enc(g[i]);
-        }
-        return;
+        for (int i = 1; i < Q; ++i)
+            nb |= (unsigned)(a.flags[n + cx(i) + cy(i) * sy + cz(i) * sz] & F_SOLID) << i;
     }
-    int x, y, z;
-    cell_coords(a.g, n, x, y, z);
+    float g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const long long off = cx(i) + cy(i) * sy + cz(i) * sz;
+        // source x - c_i = x + c_opp(i); bounce-back: f*_opp(i)(x) sits in slot i of x (layout B)
+        const long long idx = ((nb >> opp(i)) & 1u) ? (long long)i * N + n : (long long)opp(i) * N + n - off;
+        g[i] = Cd::dec(f[idx]);
+    }
+    collide<FORCE>(g, a);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const long long off = cx(i) + cy(i) * sy + cz(i) * sz;
+        const long long idx = ((nb >> i) & 1u) ? (long long)opp(i) * N + n : (long long)i * N + n + off;
+        f[idx] = Cd::enc(g[i]);
+    }
+}
+
+// Face-layer cell: every boundary rule through the general gather / scatter resolution.
+template <int S, bool FORCE>
+LBM_HD void cell_neighbor_face(const StepArgs &a, uint8_t fl, int x, int y, int z) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    T *__restrict__ f = (T *)a.f;
+    float g[Q];
     const bool fluid = !(fl & F_EQ);
     if (!fluid) {
         equilibrium_shifted(a.rho_b - 1.0f, a.ub[3 * z], a.ub[3 * z + 1], a.ub[3 * z + 2], g);
@@ -162,7 +174,10 @@ LBM_HD void read_post(const StepArgs &a, long long n, uint8_t fl, bool layoutA, 
     int x, y, z;
     cell_coords(a.g, n, x, y, z);
     if (fl & F_EQ) {
+        // the equilibrium populations as stored (and as consumed by the neighbours)
         equilibrium_shifted(a.rho_b - 1.0f, a.ub[3 * z], a.ub[3 * z + 1], a.ub[3 * z + 2], g);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) g[j] = Cd::dec(Cd::enc(g[j]));
         return;
     }
     if (!layoutA) {

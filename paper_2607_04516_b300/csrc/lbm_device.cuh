@@ -63,26 +63,32 @@ __host__ __device__ constexpr float wgt(int i) {
 }
 __host__ __device__ constexpr int cc(int i, int a) { return a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i)); }
 
-// direction with the velocity component on axis a negated (runtime argument)
-LBM_HD int mirror(int d, int a) {
-    int c0 = 0, c1 = 0, c2 = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-        if (i == d) { c0 = cx(i); c1 = cy(i); c2 = cz(i); }
-    if (a == 0) c0 = -c0; else if (a == 1) c1 = -c1; else c2 = -c2;
-    int r = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-        if (cx(i) == c0 && cy(i) == c1 && cz(i) == c2) r = i;
-    return r;
+// Runtime (non-constant) direction arithmetic from packed constants.  Component a of c_d is
+// ((PACK_a >> 2d) & 3) - 1; DIR_k holds, in 5-bit fields, the direction index of the velocity with
+// key (cx+1)*9 + (cy+1)*3 + (cz+1) (31 where that velocity is not in D3Q19), 12 keys per word.
+LBM_HD int crt(int d, int a) {
+    const unsigned long long pack = a == 0 ? 0x1489489549ull : (a == 1 ? 0x960949495ull : 0x2214894955ull);
+    return (int)((pack >> (2 * d)) & 3ull) - 1;
 }
+LBM_HD int dir_of(int vx, int vy, int vz) {
+    const int k = (vx + 1) * 9 + (vy + 1) * 3 + (vz + 1);
+    const unsigned long long w = k < 12 ? 0x9119f77e0257d1full : (k < 24 ? 0x485ff6fd6389406ull : 0x7cffull);
+    return (int)((w >> (5 * (k % 12))) & 31ull);
+}
+// direction with the velocity component on axis a negated
+LBM_HD int mirror(int d, int a) {
+    const int vx = crt(d, 0), vy = crt(d, 1), vz = crt(d, 2);
+    return dir_of(a == 0 ? -vx : vx, a == 1 ? -vy : vy, a == 2 ? -vz : vz);
+}
+LBM_HD int opp_rt(int d) { return d == 0 ? 0 : ((d & 1) ? d + 1 : d - 1); }
 
 // ---------------------------------------------------------------- cell flags
 enum : uint8_t {
     F_SOLID = 1,   // voxel solid: never updated, never read as a source
     F_EQ = 2,      // equilibrium boundary cell (on an INFLOW_EQ face layer)
-    F_SLOW = 4,    // on a face layer or next to a solid: neighbour step takes the general path
-    F_ZG = 8       // on an outflow face layer: also stores its inward populations to the side buffer
+    F_FACE = 4,    // on a face layer: the neighbour step handles it in the face blocks
+    F_ZG = 8,      // on an outflow face layer: also stores its inward populations to the side buffer
+    F_NEAR = 16    // interior cell with at least one solid neighbour (bounce-back links)
 };
 
 // ---------------------------------------------------------------- storage codecs
@@ -122,6 +128,7 @@ struct StepArgs {
     float c2x18;                // 2 (C Delta)^2 / c_s^4 = 18 C^2
     float rho_b;
     float fx, fy, fz;           // body-force density (Guo)
+    long long nface;            // cells on face layers (enumerated by face_cell_xyz)
 };
 
 // ---------------------------------------------------------------- physics (FP32)
@@ -243,21 +250,55 @@ LBM_HD Loc gather_loc_B(const Geo &G, const uint8_t *flags, int px, int py, int 
             const long long fc = face_cell(G, zg >> 1, s[0], s[1], s[2], fcells);
             return Loc{1 + zg, (long long)d * fcells + fc};
         } else {
-            return Loc{0, (long long)opp(d) * G.N + src};
+            return Loc{0, (long long)opp_rt(d) * G.N + src};
         }
     }
     // bounce-back: f*_opp(i)(p) sits in slot i of p in layout B
     return Loc{0, (long long)i * G.N + self};
 }
 
+// Up to two coordinates on one axis at which a cell consumes population j of cell p (the plain
+// downstream coordinate, or the clamped one of a free-slip reflection or a zero-gradient copy).
+struct AxisOpt {
+    int n;                 // 0, 1 or 2 options
+    int c0, c1;            // coordinates
+    bool f0, f1;           // negate this velocity component (free-slip reflection)
+    bool exit_hi;          // n == 0 because the population leaves through this outflow face
+    bool exit;
+};
+
+LBM_HD AxisOpt axis_options(const Geo &G, int a, int pa, int c) {
+    AxisOpt o{0, 0, 0, false, false, false, false};
+    const int n = dim(G, a);
+    if (c == 0) { o.n = 1; o.c0 = pa; return o; }
+    const int t = pa + c;
+    if (t >= 0 && t < n) {
+        o.n = 1; o.c0 = t;
+    } else {
+        const int hi = t >= n;
+        const int k = G.face[2 * a + hi];
+        if (k == LBM_FACE_PERIODIC) { o.n = 1; o.c0 = hi ? t - n : t + n; }
+        else if (k == LBM_FACE_FREESLIP) { o.n = 1; o.c0 = pa; o.f0 = true; }
+        else if (k == LBM_FACE_OUTFLOW_ZG) { o.exit = true; o.exit_hi = hi; }
+    }
+    // zero-gradient copy: p on an outflow layer and c pointing into the domain from that face
+    const bool zg_lo = c > 0 && pa == 0 && G.face[2 * a] == LBM_FACE_OUTFLOW_ZG;
+    const bool zg_hi = c < 0 && pa == n - 1 && G.face[2 * a + 1] == LBM_FACE_OUTFLOW_ZG;
+    if (zg_lo || zg_hi) {
+        if (o.n == 0) { o.c0 = pa; o.f0 = false; } else { o.c1 = pa; o.f1 = false; }
+        ++o.n;
+    }
+    return o;
+}
+
 // Visit every layout-A location that must receive the post-collision population j of the
-// non-solid cell p.  visit(ptr_kind, element_index): ptr_kind 0 = lattice, 1..6 = exit buffer of
-// face (ptr_kind - 1).  Returns the number of visits.
+// non-solid cell p.  visit(kind, element_index): kind 0 = lattice, 1 + face = that outflow
+// face's side buffer (exit slot).  Returns the number of visits.
 template <class V>
-LBM_HD int scatter_targets(const Geo &G, const uint8_t *flags, int px, int py,
-                                               int pz, int j, bool fluid, V &&visit) {
-    const int p[3] = {px, py, pz};
-    int t[3] = {px + cx(j), py + cy(j), pz + cz(j)};
+LBM_HD int scatter_targets(const Geo &G, const uint8_t *flags, int px, int py, int pz, int j,
+                           bool fluid, V &&visit) {
+    const int cjx = crt(j, 0), cjy = crt(j, 1), cjz = crt(j, 2);
+    const int t[3] = {px + cjx, py + cjy, pz + cjz};
     int visits = 0;
 
     // (a) bounce-back into the cell's own reversed slot
@@ -280,68 +321,74 @@ LBM_HD int scatter_targets(const Geo &G, const uint8_t *flags, int px, int py,
         if (flags[cell_of(G, r[0], r[1], r[2])] & F_SOLID) bb = true;
     }
     if (bb) {
-        visit(0, (long long)opp(j) * G.N + cell_of(G, px, py, pz));
+        visit(0, (long long)opp_rt(j) * G.N + cell_of(G, px, py, pz));
         ++visits;
     }
 
-    // (b) cells whose gather resolves to (p, j): per axis up to two coordinates
-    int opt[3][2], flip[3][2], nopt[3];
-    int exit_axis = -1, exit_hi = 0;
+    // (b) cells whose gather resolves to (p, j)
+    const AxisOpt ox = axis_options(G, 0, px, cjx);
+    const AxisOpt oy = axis_options(G, 1, py, cjy);
+    const AxisOpt oz = axis_options(G, 2, pz, cjz);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int n = dim(G, a);
-        const int c = cc(j, a);
-        nopt[a] = 0;
-        if (c == 0) {
-            opt[a][0] = p[a]; flip[a][0] = 0; nopt[a] = 1;
-            continue;
-        }
-        if (t[a] >= 0 && t[a] < n) {
-            opt[a][nopt[a]] = t[a]; flip[a][nopt[a]] = 0; ++nopt[a];
-        } else {
-            const int hi = t[a] >= n;
-            const int k = G.face[2 * a + hi];
-            if (k == LBM_FACE_PERIODIC) {
-                opt[a][nopt[a]] = hi ? t[a] - n : t[a] + n; flip[a][nopt[a]] = 0; ++nopt[a];
-            } else if (k == LBM_FACE_FREESLIP) {
-                opt[a][nopt[a]] = p[a]; flip[a][nopt[a]] = 1; ++nopt[a];
-            } else if (k == LBM_FACE_OUTFLOW_ZG && exit_axis < 0) {
-                exit_axis = a; exit_hi = hi;
+    for (int kx = 0; kx < 2; ++kx) {
+        if (kx >= ox.n) break;
+#pragma unroll
+        for (int ky = 0; ky < 2; ++ky) {
+            if (ky >= oy.n) break;
+#pragma unroll
+            for (int kz = 0; kz < 2; ++kz) {
+                if (kz >= oz.n) break;
+                const long long y = cell_of(G, kx ? ox.c1 : ox.c0, ky ? oy.c1 : oy.c0, kz ? oz.c1 : oz.c0);
+                if (flags[y] & F_SOLID) continue;
+                const bool fx = kx ? ox.f1 : ox.f0, fy = ky ? oy.f1 : oy.f0, fz = kz ? oz.f1 : oz.f0;
+                const int i = (fx || fy || fz) ? dir_of(fx ? -cjx : cjx, fy ? -cjy : cjy, fz ? -cjz : cjz) : j;
+                visit(0, (long long)i * G.N + y);
+                ++visits;
             }
         }
-        // zero-gradient copy: p on an outflow layer and c_j pointing inward from that face
-        if (c > 0 && p[a] == 0 && G.face[2 * a] == LBM_FACE_OUTFLOW_ZG) {
-            opt[a][nopt[a]] = p[a]; flip[a][nopt[a]] = 0; ++nopt[a];
-        }
-        if (c < 0 && p[a] == n - 1 && G.face[2 * a + 1] == LBM_FACE_OUTFLOW_ZG) {
-            opt[a][nopt[a]] = p[a]; flip[a][nopt[a]] = 0; ++nopt[a];
-        }
     }
-    int nb = 0;
-    if (nopt[0] && nopt[1] && nopt[2]) {
-        for (int ox = 0; ox < nopt[0]; ++ox)
-            for (int oy = 0; oy < nopt[1]; ++oy)
-                for (int oz = 0; oz < nopt[2]; ++oz) {
-                    const long long y = cell_of(G, opt[0][ox], opt[1][oy], opt[2][oz]);
-                    if (flags[y] & F_SOLID) continue;
-                    int i = j;
-                    if (flip[0][ox]) i = mirror(i, 0);
-                    if (flip[1][oy]) i = mirror(i, 1);
-                    if (flip[2][oz]) i = mirror(i, 2);
-                    visit(0, (long long)i * G.N + y);
-                    ++nb;
-                }
-    }
-    visits += nb;
 
     // (c) nothing in the lattice consumes it: a population leaving through an outflow face
-    if (visits == 0 && fluid && exit_axis >= 0) {
-        long long fcells;
-        const long long fc = face_cell(G, exit_axis, px, py, pz, fcells);
-        visit(1 + 2 * exit_axis + exit_hi, (long long)j * fcells + fc);
-        ++visits;
+    if (visits == 0 && fluid) {
+        const int ea = ox.exit ? 0 : (oy.exit ? 1 : (oz.exit ? 2 : -1));
+        if (ea >= 0) {
+            const bool ehi = ea == 0 ? ox.exit_hi : (ea == 1 ? oy.exit_hi : oz.exit_hi);
+            long long fcells;
+            const long long fc = face_cell(G, ea, px, py, pz, fcells);
+            visit(1 + 2 * ea + (ehi ? 1 : 0), (long long)j * fcells + fc);
+            ++visits;
+        }
     }
     return visits;
+}
+
+// The face-layer cells, enumerated face by face without repeats: the x faces whole, the y faces
+// without their x-edges, the z faces without their x- and y-edges.
+LBM_HD long long face_cell_count(const Geo &G) {
+    const long long xs = G.nx == 1 ? 1 : 2, ys = G.ny == 1 ? 1 : 2, zs = G.nz == 1 ? 1 : 2;
+    const long long ix = G.nx > 2 ? G.nx - 2 : 0, iy = G.ny > 2 ? G.ny - 2 : 0;
+    return xs * G.ny * G.nz + ys * ix * G.nz + zs * ix * iy;
+}
+LBM_HD void face_cell_xyz(const Geo &G, long long t, int &x, int &y, int &z) {
+    const long long xs = G.nx == 1 ? 1 : 2, ys = G.ny == 1 ? 1 : 2;
+    const long long ix = G.nx > 2 ? G.nx - 2 : 0, iy = G.ny > 2 ? G.ny - 2 : 0;
+    const long long nxf = (long long)G.ny * G.nz;
+    if (t < xs * nxf) {
+        const long long side = t / nxf, r = t - side * nxf;
+        x = side ? G.nx - 1 : 0; y = (int)(r % G.ny); z = (int)(r / G.ny);
+        return;
+    }
+    t -= xs * nxf;
+    const long long nyf = ix * G.nz;
+    if (t < ys * nyf) {
+        const long long side = t / nyf, r = t - side * nyf;
+        y = side ? G.ny - 1 : 0; x = 1 + (int)(r % ix); z = (int)(r / ix);
+        return;
+    }
+    t -= ys * nyf;
+    const long long nzf = ix * iy;
+    const long long side = t / nzf, r = t - side * nzf;
+    z = side ? G.nz - 1 : 0; x = 1 + (int)(r % ix); y = 1 + (int)(r / ix);
 }
 
 LBM_HD void cell_coords(const Geo &G, long long n, int &x, int &y, int &z);

@@ -39,11 +39,25 @@ __global__ void __launch_bounds__(kBlock) k_step_local(StepArgs a) {
     cell_local<S, FORCE>(a, n);
 }
 
+// Blocks [0, interior_blocks) cover the lattice and update its interior cells; the remaining
+// blocks update the face-layer cells, so no warp mixes the two paths.
 template <int S, bool FORCE>
-__global__ void __launch_bounds__(kBlock) k_step_neighbor(StepArgs a) {
-    const long long G_N = a.g.N;
-    LBM_CELL_INDEX();
-    cell_neighbor<S, FORCE>(a, n);
+__global__ void __launch_bounds__(kBlock) k_step_neighbor(StepArgs a, unsigned interior_blocks) {
+    if (blockIdx.x < interior_blocks) {
+        const long long n = (long long)blockIdx.x * kBlock + threadIdx.x;
+        if (n >= a.g.N) return;
+        const uint8_t fl = a.flags[n];
+        if (fl & (F_SOLID | F_FACE)) return;
+        cell_neighbor_interior<S, FORCE>(a, n, fl);
+    } else {
+        const long long t = (long long)(blockIdx.x - interior_blocks) * kBlock + threadIdx.x;
+        if (t >= a.nface) return;
+        int x, y, z;
+        face_cell_xyz(a.g, t, x, y, z);
+        const uint8_t fl = a.flags[cell_of(a.g, x, y, z)];
+        if (fl & F_SOLID) return;
+        cell_neighbor_face<S, FORCE>(a, fl, x, y, z);
+    }
 }
 
 template <int S>
@@ -186,7 +200,10 @@ cudaError_t launch_init(int store, const StepArgs &a, const float *rho, const fl
 
 template <int S, bool FORCE>
 static void step_t(bool neighbor, const StepArgs &a, cudaStream_t s) {
-    if (neighbor) k_step_neighbor<S, FORCE><<<blocks_for(a.g.N), kBlock, 0, s>>>(a);
+    if (neighbor) {
+        const unsigned ib = blocks_for(a.g.N);
+        k_step_neighbor<S, FORCE><<<ib + blocks_for(a.nface), kBlock, 0, s>>>(a, ib);
+    }
     else k_step_local<S, FORCE><<<blocks_for(a.g.N), kBlock, 0, s>>>(a);
 }
 template <int S>

@@ -171,7 +171,8 @@ def city_case(nx: int = 400, ny: int = 400, nz: int = 80, seed: int = 1, dir_see
     theta = direction_from_seed(seed if dir_seed is None else dir_seed)
     speed = power_law_levels(nz, u_ref, z_ref, alpha)
     faces = faces_for_direction(theta)
-    u0 = perturb(profile_field(speed, theta, solid.shape), solid, noise * u_ref, seed + 1000)
+    u0 = (perturb(profile_field(speed, theta, solid.shape), solid, noise * u_ref, seed + 1000)
+          if noise > 0 else None)
     return Case(f"city{nx}x{ny}x{nz}", solid, faces, tau, cs, speed, theta, u0=u0,
                 meta={"seed": seed, **info})
 

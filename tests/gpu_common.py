@@ -64,10 +64,11 @@ def rel_l2(a, b, mask):
     return float(np.linalg.norm((a - b)[mask]) / np.linalg.norm(b[mask]))
 
 
-def oracle_one_step_planes(g_lib: np.ndarray, kind: np.ndarray, faces, ub: np.ndarray, tau: float,
+def oracle_one_step_planes(g_planes: dict, kind: np.ndarray, faces, ub: np.ndarray, tau: float,
                            cs: float, force, rho_b: float, planes, perm):
-    """Oracle step from a given post-collision state (library-order shifted FP32 populations of
-    planes z-1..z+1 for every requested z) to the next one, on the requested planes only.
+    """Oracle step from a given post-collision state (``g_planes[z]``: library-order shifted FP32
+    populations (19, ny, nx) of planes z-1..z+1 for every requested z) to the next one, on the
+    requested planes only.
     Returns {z: F_next plane (19, ny, nx) in oracle order}.  Gathers of plane z reach z +- 1 only,
     so a three-plane slab (with the true z face where it touches the lattice boundary) is exact."""
     _, wo, _ = orc.lattice()
@@ -76,7 +77,7 @@ def oracle_one_step_planes(g_lib: np.ndarray, kind: np.ndarray, faces, ub: np.nd
     for z in planes:
         za, zb = max(z - 1, 0), min(z + 1, nz - 1)
         sl = slice(za, zb + 1)
-        G = g_lib[:, sl].astype(np.float64)[perm]            # oracle order
+        G = np.stack([g_planes[p] for p in range(za, zb + 1)], axis=1).astype(np.float64)[perm]
         F = G + wo[:, None, None, None]
         kk = np.ascontiguousarray(kind[sl])
         F[:, kk == orc.SOLID] = 0.0
