@@ -24,7 +24,7 @@ size_t store_bytes(int store) { return store == LBM_F32 ? 4 : 2; }
 
 // Regions of the caller's workspace, in bytes from its start.
 struct Layout {
-    size_t f, flags, ub, side[6], part, diag, total;
+    size_t f, flags, info, ub, side[6], part, diag, total;
     long long side_cells[6];
 };
 
@@ -61,6 +61,7 @@ Layout make_layout(int nx, int ny, int nz, const lbm_params *p) {
     size_t off = 0;
     L.f = off; off = align_up(off + (size_t)Q * N * sb);
     L.flags = off; off = align_up(off + (size_t)N);
+    L.info = off; off = align_up(off + (size_t)N * sizeof(uint32_t));
     L.ub = off; off = align_up(off + (size_t)nz * 3 * sizeof(float));
     const long long fc[3] = {(long long)ny * nz, (long long)nx * nz, (long long)nx * ny};
     for (int k = 0; k < 6; ++k) {
@@ -113,6 +114,7 @@ StepArgs args_of(const lbm_domain *d) {
     StepArgs a{};
     a.f = d->ws + d->L.f;
     a.flags = (const uint8_t *)(d->ws + d->L.flags);
+    a.info = (const uint32_t *)(d->ws + d->L.info);
     a.ub = (const float *)(d->ws + d->L.ub);
     for (int k = 0; k < 6; ++k) a.side[k] = d->L.side_cells[k] ? d->ws + d->L.side[k] : nullptr;
     a.g.N = d->N;
@@ -125,6 +127,16 @@ StepArgs args_of(const lbm_domain *d) {
     a.rho_b = d->p.rho_b;
     a.fx = d->p.force[0]; a.fy = d->p.force[1]; a.fz = d->p.force[2];
     a.nface = face_cell_count(a.g);
+    const size_t sb = store_bytes(d->p.store);
+    for (int i = 0; i < Q; ++i) {
+        a.plane[i] = (char *)a.f + (size_t)i * (size_t)d->N * sb;
+        a.off[i] = (int)(cx(i) + cy(i) * a.g.sy + cz(i) * a.g.sz);
+    }
+    a.zwrap = (int)(d->nz * a.g.sz);
+    const long long xs = d->nx == 1 ? 1 : 2, ys = d->ny == 1 ? 1 : 2;
+    const long long ix = d->nx > 2 ? d->nx - 2 : 0;
+    a.zface_begin = xs * d->ny * d->nz + ys * ix * d->nz;
+    a.zfast = zfast_mask(a.g);
     return a;
 }
 
@@ -200,7 +212,7 @@ lbm_status lbm_create_domain(const uint8_t *solid, int nx, int ny, int nz, const
     uint8_t *mask_dev = (uint8_t *)(d->ws + L.f);
     lbm_status st = cuda_check(d, cudaMemcpyAsync(mask_dev, solid, (size_t)d->N, cudaMemcpyHostToDevice,
                                                   d->stream), "mask upload");
-    if (st == LBM_OK) st = cuda_check(d, launch_flags(mask_dev, (uint8_t *)(d->ws + L.flags), a.g, d->stream), "flags kernel");
+    if (st == LBM_OK) st = cuda_check(d, launch_flags(mask_dev, (uint8_t *)(d->ws + L.flags), (uint32_t *)(d->ws + L.info), a.g, d->stream), "flags kernel");
     if (st == LBM_OK) st = cuda_check(d, cudaMemsetAsync(d->ws + L.ub, 0, (size_t)nz * 3 * sizeof(float), d->stream), "profile clear");
     for (int k = 0; k < 6 && st == LBM_OK; ++k)
         if (L.side_cells[k])

@@ -7,35 +7,48 @@
 namespace lbm {
 
 // ---------------------------------------------------------------- flags from the solid mask
-LBM_HD void cell_flags(const uint8_t *__restrict__ mask, uint8_t *__restrict__ flags, const Geo &G,
-                       long long n) {
-    if (mask[n]) { flags[n] = F_SOLID; return; }
+// Cell kind bits and, for cells that use the store-side bounce-back convention (F_REDIR: interior
+// cells, and cells of a no-slip / free-slip z layer with interior x and y, that have a solid
+// neighbour), the mask of solid neighbours x + c_i.
+LBM_HD void cell_flags(const uint8_t *__restrict__ mask, uint8_t *__restrict__ flags,
+                       uint32_t *__restrict__ info, const Geo &G, long long n) {
+    if (mask[n]) { flags[n] = F_SOLID; info[n] = F_SOLID; return; }
     int x, y, z;
     cell_coords(G, n, x, y, z);
     const bool lo[3] = {x == 0, y == 0, z == 0};
     const bool hi[3] = {x == G.nx - 1, y == G.ny - 1, z == G.nz - 1};
-    bool eq = false, onface = false;
+    bool eq = false, onface = false, zgl = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         onface |= lo[a] | hi[a];
-        eq |= (lo[a] && G.face[2 * a] == LBM_FACE_INFLOW_EQ) ||
-              (hi[a] && G.face[2 * a + 1] == LBM_FACE_INFLOW_EQ);
-    }
-    bool zgl = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
+        eq |= (lo[a] && G.face[2 * a] == LBM_FACE_INFLOW_EQ) || (hi[a] && G.face[2 * a + 1] == LBM_FACE_INFLOW_EQ);
         zgl |= (lo[a] && G.face[2 * a] == LBM_FACE_OUTFLOW_ZG) || (hi[a] && G.face[2 * a + 1] == LBM_FACE_OUTFLOW_ZG);
-    uint8_t fl = zgl ? F_ZG : 0;
-    if (onface) fl |= F_FACE;
-    if (eq) {
-        fl |= F_EQ;
-    } else if (!onface) {   // interior cell: all 18 neighbours are in range
-        bool near = false;
+    }
+    uint8_t fl = (zgl ? F_ZG : 0) | (onface ? F_FACE : 0) | (eq ? F_EQ : 0);
+    const bool xy_interior = !lo[0] && !hi[0] && !lo[1] && !hi[1];
+    const int zf = zfast_mask(G);
+    const bool layer_path = xy_interior && ((lo[2] && (zf & 1)) || (hi[2] && (zf & 2))) && !(lo[2] && hi[2]);
+    uint32_t nb = 0;
+    if (!eq && ((!onface) || layer_path)) {
 #pragma unroll
-        for (int i = 1; i < Q; ++i) near |= mask[n + cx(i) + cy(i) * G.sy + cz(i) * G.sz] != 0;
-        if (near) fl |= F_NEAR;
+        for (int i = 1; i < Q; ++i) {
+            const int zz = z + cz(i);
+            if (zz < 0 || zz >= G.nz) continue;   // beyond a z face: handled by the face rule
+            nb |= (uint32_t)(mask[cell_of(G, x + cx(i), y + cy(i), zz)] != 0) << i;
+        }
+        if (nb) fl |= F_REDIR;
     }
     flags[n] = fl;
+    info[n] = fl | (nb << 8);
+}
+
+// Store-side bounce-back: a post-collision population f*_k of a cell x whose neighbour x + c_k is
+// solid is consumed by x itself, as f_opp(k), in the next neighbour step.  Instead of its own slot
+// opp(k), an F_REDIR cell stores it into slot k of that solid neighbour (memory nobody else
+// touches), so that the next neighbour step's gather of direction opp(k) is the plain pull from
+// x - c_opp(k) = x + c_k.  Layout-B location of f*_k(x):
+LBM_HD long long post_loc_B(const StepArgs &a, long long n, int k, unsigned nb) {
+    return ((nb >> k) & 1u) ? (long long)k * a.g.N + n + a.off[k] : (long long)opp_rt(k) * a.g.N + n;
 }
 
 // ---------------------------------------------------------------- equilibrium initialisation
@@ -47,11 +60,9 @@ LBM_HD void cell_init(const StepArgs &a, long long n, const float *__restrict__ 
     const uint8_t fl = a.flags[n];
     T *f = (T *)a.f;
     const long long N = a.g.N;
-    if (fl & F_SOLID) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) f[(long long)i * N + n] = Cd::enc(0.0f);
-        return;
-    }
+    // solid cells own no state: their slots only receive store-side bounce-back populations of
+    // fluid neighbours (written below by those neighbours), so they are left alone here
+    if (fl & F_SOLID) return;
     const int z = (int)(n / a.g.sz);
     float drho, ux, uy, uz;
     if (fl & F_EQ) {
@@ -64,8 +75,10 @@ LBM_HD void cell_init(const StepArgs &a, long long n, const float *__restrict__ 
     }
     float g[Q];
     equilibrium_shifted(drho, ux, uy, uz, g);
+    const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[(long long)opp(i) * N + n] = Cd::enc(g[i]);   // layout B
+    for (int i = 0; i < Q; ++i)   // layout B
+        f[((nb >> i) & 1u) ? (long long)i * N + n + a.off[i] : (long long)opp(i) * N + n] = Cd::enc(g[i]);
     if (fl & F_ZG) {
         int x, y, zz;
         cell_coords(a.g, n, x, y, zz);
@@ -75,24 +88,32 @@ LBM_HD void cell_init(const StepArgs &a, long long n, const float *__restrict__ 
 
 // ---------------------------------------------------------------- local step: A -> B
 template <int S, bool FORCE>
-LBM_HD void cell_local(const StepArgs &a, long long n) {
+LBM_HD void cell_local(const StepArgs &a, int n) {
     using Cd = Codec<S>;
     using T = typename Cd::T;
     const uint8_t fl = a.flags[n];
     if (fl & F_SOLID) return;
-    T *__restrict__ f = (T *)a.f;
-    const long long N = a.g.N;
+    T *const *P = (T *const *)a.plane;
     float g[Q];
     if (fl & F_EQ) {
         const int z = (int)(n / a.g.sz);
         equilibrium_shifted(a.rho_b - 1.0f, a.ub[3 * z], a.ub[3 * z + 1], a.ub[3 * z + 2], g);
     } else {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = Cd::dec(f[(long long)i * N + n]);
+        for (int i = 0; i < Q; ++i) g[i] = Cd::dec(P[i][n]);
         collide<FORCE>(g, a);
     }
+    if (fl & F_REDIR) {
+        const unsigned nb = a.info[n] >> 8;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[(long long)opp(i) * N + n] = Cd::enc(g[i]);
+        for (int i = 0; i < Q; ++i) {
+            const bool bb = (nb >> i) & 1u;
+            (bb ? P[i] : P[opp(i)])[bb ? n + a.off[i] : n] = Cd::enc(g[i]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) P[opp(i)][n] = Cd::enc(g[i]);
+    }
     if (fl & F_ZG) {
         int x, y, z;
         cell_coords(a.g, n, x, y, z);
@@ -101,36 +122,86 @@ LBM_HD void cell_local(const StepArgs &a, long long n) {
 }
 
 // ---------------------------------------------------------------- neighbour step: B -> A
-// Interior cell (on no face layer): pull from x - c_i and push to x + c_i; a solid neighbour turns
-// the link into bounce-back (read / write the cell's own reversed slot).  The 18 neighbour flags
-// are loaded only for cells marked F_NEAR.
+// Interior cell (on no face layer): pull from x - c_i and push to x + c_i.  A solid neighbour
+// needs nothing on the gather side (store-side bounce-back, see post_loc_B); on the scatter side a
+// population heading into a solid goes to the cell's own reversed slot.  No load depends on
+// another load.
 template <int S, bool FORCE>
-LBM_HD void cell_neighbor_interior(const StepArgs &a, long long n, uint8_t fl) {
+LBM_HD void cell_neighbor_interior(const StepArgs &a, int n, uint8_t fl) {
     using Cd = Codec<S>;
     using T = typename Cd::T;
-    T *__restrict__ f = (T *)a.f;
-    const long long N = a.g.N;
-    const long long sy = a.g.sy, sz = a.g.sz;
-    unsigned nb = 0;   // bit i: the neighbour x + c_i is solid
-    if (fl & F_NEAR) {
+    T *const *P = (T *const *)a.plane;
+    float g[Q];
 #pragma unroll
-        for (int i = 1; i < Q; ++i)
-            nb |= (unsigned)(a.flags[n + cx(i) + cy(i) * sy + cz(i) * sz] & F_SOLID) << i;
+    for (int i = 0; i < Q; ++i) g[i] = Cd::dec(P[opp(i)][n - a.off[i]]);
+    const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
+    collide<FORCE>(g, a);
+    if (nb) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const bool bb = (nb >> i) & 1u;
+            (bb ? P[opp(i)] : P[i])[bb ? n : n + a.off[i]] = Cd::enc(g[i]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) P[i][n + a.off[i]] = Cd::enc(g[i]);
     }
+}
+
+// Cell of the ground or top layer with interior x and y, when that z face is no-slip or
+// free-slip: the interior rules plus, for the links crossing the face, bounce-back (no-slip) or
+// specular reflection within the layer (free-slip).  Populations stored by such a cell toward the
+// face stay in its own slots (no memory beyond the face), so those gathers read the cell itself.
+template <int S, bool FORCE>
+LBM_HD void cell_neighbor_zlayer(const StepArgs &a, int n, uint8_t fl, bool top) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    T *const *P = (T *const *)a.plane;
+    const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
+    const bool noslip = a.g.face[top ? 5 : 4] == LBM_FACE_NOSLIP;
+    const int cout = top ? 1 : -1;        // c_z of the links leaving through this face
     float g[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const long long off = cx(i) + cy(i) * sy + cz(i) * sz;
-        // source x - c_i = x + c_opp(i); bounce-back: f*_opp(i)(x) sits in slot i of x (layout B)
-        const long long idx = ((nb >> opp(i)) & 1u) ? (long long)i * N + n : (long long)opp(i) * N + n - off;
-        g[i] = Cd::dec(f[idx]);
+        const T *p;
+        int idx;
+        if (cz(i) == -cout) {             // the source x - c_i lies beyond the face
+            if (noslip) {
+                p = P[i]; idx = n;
+            } else {
+                // source (x - c_x, y - c_y) in this layer, mirrored direction; bounce-back if solid
+                const int k = (cx(i) == 0 && cy(i) == 0) ? 0 : dir_c(-cx(i), -cy(i), 0);
+                const int d = dir_c(cx(i), cy(i), -cz(i));
+                const bool bb = k != 0 && ((nb >> k) & 1u);
+                p = bb ? P[i] : P[opp(d)];
+                idx = bb ? n : n + a.off[k];
+            }
+        } else {
+            p = P[opp(i)]; idx = n - a.off[i];
+        }
+        g[i] = Cd::dec(p[idx]);
     }
     collide<FORCE>(g, a);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const long long off = cx(i) + cy(i) * sy + cz(i) * sz;
-        const long long idx = ((nb >> i) & 1u) ? (long long)opp(i) * N + n : (long long)i * N + n + off;
-        f[idx] = Cd::enc(g[i]);
+    for (int j = 0; j < Q; ++j) {
+        T *p;
+        int idx;
+        if (cz(j) == cout) {              // the target x + c_j lies beyond the face
+            if (noslip) {
+                p = P[opp(j)]; idx = n;
+            } else {
+                const int k = (cx(j) == 0 && cy(j) == 0) ? 0 : dir_c(cx(j), cy(j), 0);
+                const int m = dir_c(cx(j), cy(j), -cz(j));
+                const bool bb = k != 0 && ((nb >> k) & 1u);
+                p = bb ? P[opp(j)] : P[m];
+                idx = bb ? n : n + a.off[k];
+            }
+        } else {
+            const bool bb = (nb >> j) & 1u;
+            p = bb ? P[opp(j)] : P[j];
+            idx = bb ? n : n + a.off[j];
+        }
+        p[idx] = Cd::enc(g[j]);
     }
 }
 
@@ -170,7 +241,6 @@ LBM_HD void read_post(const StepArgs &a, long long n, uint8_t fl, bool layoutA, 
     using Cd = Codec<S>;
     using T = typename Cd::T;
     const T *f = (const T *)a.f;
-    const long long N = a.g.N;
     int x, y, z;
     cell_coords(a.g, n, x, y, z);
     if (fl & F_EQ) {
@@ -181,8 +251,9 @@ LBM_HD void read_post(const StepArgs &a, long long n, uint8_t fl, bool layoutA, 
         return;
     }
     if (!layoutA) {
+        const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
 #pragma unroll
-        for (int j = 0; j < Q; ++j) g[j] = Cd::dec(f[(long long)opp(j) * N + n]);
+        for (int j = 0; j < Q; ++j) g[j] = Cd::dec(f[post_loc_B(a, n, j, nb)]);
         return;
     }
 #pragma unroll

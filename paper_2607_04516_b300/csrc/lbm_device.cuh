@@ -62,6 +62,10 @@ __host__ __device__ constexpr float wgt(int i) {
     return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
 }
 __host__ __device__ constexpr int cc(int i, int a) { return a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i)); }
+// direction index of velocity (vx, vy, vz), compile-time (-1 if not a D3Q19 velocity)
+__host__ __device__ constexpr int dir_c(int vx, int vy, int vz, int i = 0) {
+    return i == Q ? -1 : ((cx(i) == vx && cy(i) == vy && cz(i) == vz) ? i : dir_c(vx, vy, vz, i + 1));
+}
 
 // Runtime (non-constant) direction arithmetic from packed constants.  Component a of c_d is
 // ((PACK_a >> 2d) & 3) - 1; DIR_k holds, in 5-bit fields, the direction index of the velocity with
@@ -88,7 +92,7 @@ enum : uint8_t {
     F_EQ = 2,      // equilibrium boundary cell (on an INFLOW_EQ face layer)
     F_FACE = 4,    // on a face layer: the neighbour step handles it in the face blocks
     F_ZG = 8,      // on an outflow face layer: also stores its inward populations to the side buffer
-    F_NEAR = 16    // interior cell with at least one solid neighbour (bounce-back links)
+    F_REDIR = 16   // has a solid neighbour and stores bounce-back links into it (see cell_local)
 };
 
 // ---------------------------------------------------------------- storage codecs
@@ -121,6 +125,8 @@ struct Geo {
 struct StepArgs {
     void *f;                    // 19 * N populations (storage type)
     const uint8_t *flags;       // N
+    const uint32_t *info;       // N: flag byte | solid-neighbour mask << 8 (bit 8 + i: x + c_i solid)
+                                //    (set for F_REDIR cells)
     const float *ub;            // nz * 3 inflow velocity per height
     void *side[6];              // per outflow face: 19 * (face cells) side/exit buffer, else null
     Geo g;
@@ -129,7 +135,20 @@ struct StepArgs {
     float rho_b;
     float fx, fy, fz;           // body-force density (Guo)
     long long nface;            // cells on face layers (enumerated by face_cell_xyz)
+    void *plane[Q];             // base address of population plane i (= f + i * N elements)
+    int off[Q];                 // cell offset of the neighbour x + c_i (c_x + c_y sy + c_z sz)
+    int zwrap;                  // nz * sz: cell offset of a periodic wrap along z
+    long long zface_begin;      // first face-enumeration index of the z faces (interior x, y)
+    int zfast;                  // bit 0 / bit 1: the z- / z+ face cells take the layer path
 };
+
+// The z face layers whose cells (with interior x and y) take the layer path: no-slip or free-slip
+// faces on a lattice at least 3 x 3 x 2.
+LBM_HD int zfast_mask(const Geo &G) {
+    if (G.nz < 2 || G.nx < 3 || G.ny < 3) return 0;
+    const auto ok = [](int k) { return k == LBM_FACE_NOSLIP || k == LBM_FACE_FREESLIP; };
+    return (ok(G.face[4]) ? 1 : 0) | (ok(G.face[5]) ? 2 : 0);
+}
 
 // ---------------------------------------------------------------- physics (FP32)
 // Equilibrium in shifted form: g^eq_i = f^eq_i - w_i = w_i (drho + rho (3 c.u + 4.5 (c.u)^2

@@ -7,6 +7,15 @@
 // step's x-shifted planes straddle one extra 32-byte sector that the next warp uses).
 #include <cuda_runtime.h>
 
+// resident 256-thread blocks per SM the step kernels are compiled for (caps registers at
+// 65536 / (256 * blocks)); chosen by measurement on B300
+#ifndef LBM_MIN_BLOCKS_LOCAL
+#define LBM_MIN_BLOCKS_LOCAL 4
+#endif
+#ifndef LBM_MIN_BLOCKS_NEIGHBOR
+#define LBM_MIN_BLOCKS_NEIGHBOR 4
+#endif
+
 #include "lbm_cell.cuh"
 #include "lbm_internal.h"
 
@@ -19,10 +28,11 @@ constexpr int kBlock = 256;
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; \
     if (n >= G_N) return;
 
-__global__ void k_flags(const uint8_t *__restrict__ mask, uint8_t *__restrict__ flags, Geo G) {
+__global__ void k_flags(const uint8_t *__restrict__ mask, uint8_t *__restrict__ flags,
+                        uint32_t *__restrict__ info, Geo G) {
     const long long G_N = G.N;
     LBM_CELL_INDEX();
-    cell_flags(mask, flags, G, n);
+    cell_flags(mask, flags, info, G, n);
 }
 
 template <int S>
@@ -33,29 +43,36 @@ __global__ void k_init(StepArgs a, const float *__restrict__ rho, const float *_
 }
 
 template <int S, bool FORCE>
-__global__ void __launch_bounds__(kBlock) k_step_local(StepArgs a) {
-    const long long G_N = a.g.N;
-    LBM_CELL_INDEX();
+__global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_LOCAL) k_step_local(StepArgs a) {
+    const int n = (int)(blockIdx.x * kBlock + threadIdx.x);
+    if (n >= a.g.N) return;
     cell_local<S, FORCE>(a, n);
 }
 
-// Blocks [0, interior_blocks) cover the lattice and update its interior cells; the remaining
-// blocks update the face-layer cells, so no warp mixes the two paths.
+// Blocks [0, face_blocks) update the face-layer cells (general boundary resolution, ALU heavy);
+// the remaining blocks cover the lattice and update its interior cells.  Face blocks go first so
+// that their arithmetic overlaps the memory traffic of the interior blocks, and no warp mixes the
+// two paths.
 template <int S, bool FORCE>
-__global__ void __launch_bounds__(kBlock) k_step_neighbor(StepArgs a, unsigned interior_blocks) {
-    if (blockIdx.x < interior_blocks) {
-        const long long n = (long long)blockIdx.x * kBlock + threadIdx.x;
+__global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_NEIGHBOR) k_step_neighbor(StepArgs a, unsigned face_blocks) {
+    if (blockIdx.x >= face_blocks) {
+        const int n = (int)((blockIdx.x - face_blocks) * kBlock + threadIdx.x);
         if (n >= a.g.N) return;
         const uint8_t fl = a.flags[n];
         if (fl & (F_SOLID | F_FACE)) return;
         cell_neighbor_interior<S, FORCE>(a, n, fl);
     } else {
-        const long long t = (long long)(blockIdx.x - interior_blocks) * kBlock + threadIdx.x;
+        const long long t = (long long)blockIdx.x * kBlock + threadIdx.x;
         if (t >= a.nface) return;
         int x, y, z;
         face_cell_xyz(a.g, t, x, y, z);
-        const uint8_t fl = a.flags[cell_of(a.g, x, y, z)];
+        const int n = (int)cell_of(a.g, x, y, z);
+        const uint8_t fl = a.flags[n];
         if (fl & F_SOLID) return;
+        if (t >= a.zface_begin && ((a.zfast >> (z == 0 ? 0 : 1)) & 1)) {
+            cell_neighbor_zlayer<S, FORCE>(a, n, fl, z != 0);
+            return;
+        }
         cell_neighbor_face<S, FORCE>(a, fl, x, y, z);
     }
 }
@@ -180,8 +197,8 @@ __global__ void __launch_bounds__(kBlock) k_reduce_final(const double *__restric
 // ---------------------------------------------------------------- launchers
 static inline unsigned blocks_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
-cudaError_t launch_flags(const uint8_t *mask, uint8_t *flags, const Geo &G, cudaStream_t s) {
-    k_flags<<<blocks_for(G.N), kBlock, 0, s>>>(mask, flags, G);
+cudaError_t launch_flags(const uint8_t *mask, uint8_t *flags, uint32_t *info, const Geo &G, cudaStream_t s) {
+    k_flags<<<blocks_for(G.N), kBlock, 0, s>>>(mask, flags, info, G);
     return cudaGetLastError();
 }
 
@@ -201,8 +218,8 @@ cudaError_t launch_init(int store, const StepArgs &a, const float *rho, const fl
 template <int S, bool FORCE>
 static void step_t(bool neighbor, const StepArgs &a, cudaStream_t s) {
     if (neighbor) {
-        const unsigned ib = blocks_for(a.g.N);
-        k_step_neighbor<S, FORCE><<<ib + blocks_for(a.nface), kBlock, 0, s>>>(a, ib);
+        const unsigned fb = blocks_for(a.nface);
+        k_step_neighbor<S, FORCE><<<fb + blocks_for(a.g.N), kBlock, 0, s>>>(a, fb);
     }
     else k_step_local<S, FORCE><<<blocks_for(a.g.N), kBlock, 0, s>>>(a);
 }

@@ -236,7 +236,8 @@ def test_watchdog_reports_nonfinite_state():
     case = synth.cube_case(nx=16, ny=16, nz=8)
     dom = gpu_domain(case, "f32", watchdog_every=2)
     u = case.u0.astype(np.float32).copy()
-    u[4, 8, 8, 0] = np.nan                          # a corrupt input cell, rejected by nothing
+    u[4, 2, 2, 0] = np.nan                          # a corrupt fluid input cell, rejected by nothing
+    assert not case.solid[4, 2, 2]
     dom.init_fields(None, u)
     with pytest.raises(lbm.LbmError) as e:
         dom.step(4)
