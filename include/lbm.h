@@ -167,6 +167,20 @@ int lbm_direction_table(int *c, float *w);
  * Synchronises the domain's stream. */
 lbm_status lbm_diagnostics(lbm_domain *d, double *out);
 
+/* The same reductions as lbm_diagnostics, for callers that must not allocate device memory and
+ * cannot wait on the host (a stream-ordered serving or assimilation loop under a fixed memory
+ * budget, or a workspace sized without reduction scratch).  No counterpart in the paper.
+ *   out  DEVICE double[4], written asynchronously on the domain's stream (same meaning as
+ *        lbm_diagnostics' out); nothing is copied to the host and the stream is not synchronised
+ * Allocates nothing: the partial sums live in a fixed 512 KiB array inside the library (kept by
+ * every GPU that loads it until the process exits), which limits the lattice to 2^28 cells;
+ * larger lattices return LBM_EINVAL.  All calls share that array: calls whose kernels overlap on
+ * the GPU (different streams or host threads) race, so keep them in one stream order.  The first
+ * call on a device looks up the array's device address; make it before any stream capture.  The
+ * partial sums are added in a different order than in lbm_diagnostics, so the two agree to FP64
+ * rounding, not bit for bit. */
+lbm_status lbm_diagnostics_noalloc(lbm_domain *d, double *out);
+
 /* Message of the last failed call on this domain ("" if none).  Never NULL. */
 const char *lbm_last_error(const lbm_domain *d);
 

@@ -14,7 +14,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liblbm.so")
-SOURCES = [os.path.join(CSRC, "lbm_kernels.cu"), os.path.join(CSRC, "lbm_capi.cu")]
+SOURCES = [os.path.join(CSRC, "lbm_kernels.cu"), os.path.join(CSRC, "lbm_capi.cu"),
+           os.path.join(CSRC, "lbm_noalloc.cu")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -146,6 +146,13 @@ bool has_force(const lbm_domain *d) {
 
 }  // namespace
 
+namespace lbm {
+DomainView domain_view(const lbm_domain *d) {
+    return DomainView{args_of(d), d->p.store, (d->t & 1) != 0, d->stream};
+}
+lbm_status domain_fail(lbm_domain *d, lbm_status st, const char *msg) { return fail(d, st, "%s", msg); }
+}  // namespace lbm
+
 extern "C" {
 
 lbm_status lbm_params_default(lbm_params *p) {

@@ -20,4 +20,14 @@ cudaError_t launch_export(int store, const StepArgs &a, bool layoutA, float *out
 cudaError_t launch_reduce(int store, const StepArgs &a, bool layoutA, double *part, double *out,
                           cudaStream_t s);
 
+// Read-only view of a domain for entry points defined outside lbm_capi.cu.
+struct DomainView {
+    StepArgs args;
+    int store;
+    bool layoutA;
+    cudaStream_t stream;
+};
+DomainView domain_view(const lbm_domain *d);
+lbm_status domain_fail(lbm_domain *d, lbm_status st, const char *msg);
+
 }  // namespace lbm

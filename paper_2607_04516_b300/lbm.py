@@ -53,6 +53,7 @@ SIGNATURES = {
     "lbm_export_populations": (_I, [_P, _P]),
     "lbm_direction_table": (_I, [_P, _P]),
     "lbm_diagnostics": (_I, [_P, _P]),
+    "lbm_diagnostics_noalloc": (_I, [_P, _P]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
     "lbm_destroy": (None, [_P]),
 }
@@ -173,6 +174,13 @@ def lbm_diagnostics(dom) -> dict:
     out = np.zeros(4, np.float64)
     _check(load().lbm_diagnostics(dom, out.ctypes.data), dom)
     return {"mass": out[0], "net_flux": out[1], "umax": out[2], "nonfinite": int(out[3])}
+
+
+def lbm_diagnostics_noalloc(dom, out):
+    """``out``: CUDA float64 tensor of 4 elements, filled asynchronously on the domain's stream."""
+    if out.dtype.itemsize != 8 or out.numel() < 4 or not out.is_cuda:
+        raise ValueError("out must be a CUDA float64 tensor with 4 elements")
+    _check(load().lbm_diagnostics_noalloc(dom, _ptr(out)), dom)
 
 
 def lbm_destroy(dom):
