@@ -59,7 +59,12 @@ Layout make_layout(int nx, int ny, int nz, const lbm_params *p) {
     const long long N = (long long)nx * ny * nz;
     const size_t sb = store_bytes(p->store);
     size_t off = 0;
-    L.f = off; off = align_up(off + (size_t)Q * N * sb);
+    // populations between two guards of one z-plane + one row + 512 cells: the step kernels issue
+    // their population loads before reading the cell flags, so a load for a cell that turns out to
+    // be solid or on a face may reach up to that far before the first or past the last plane (its
+    // value is discarded)
+    const size_t guard = align_up(((size_t)nx * ny + nx + 512) * sb);
+    L.f = guard; off = align_up(guard + (size_t)Q * N * sb + guard);
     L.flags = off; off = align_up(off + (size_t)N);
     L.info = off; off = align_up(off + (size_t)N * sizeof(uint32_t));
     L.ub = off; off = align_up(off + (size_t)nz * 3 * sizeof(float));
@@ -137,6 +142,7 @@ StepArgs args_of(const lbm_domain *d) {
     const long long ix = d->nx > 2 ? d->nx - 2 : 0;
     a.zface_begin = xs * d->ny * d->nz + ys * ix * d->nz;
     a.zfast = zfast_mask(a.g);
+    a.pack16 = (d->p.store != LBM_F32 && d->N % 2 == 0 && d->nx % 2 == 0) ? 1 : 0;
     return a;
 }
 

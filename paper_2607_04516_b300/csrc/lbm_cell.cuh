@@ -4,7 +4,15 @@
 
 #include "lbm_device.cuh"
 
+// 16-bit storage: evaluate the collision on opposite pairs (1) or direction by direction (0);
+// chosen by measurement on B300
+#ifndef LBM_PAIRS16
+#define LBM_PAIRS16 1
+#endif
+
 namespace lbm {
+
+constexpr bool kPairs16 = LBM_PAIRS16 != 0;
 
 // ---------------------------------------------------------------- flags from the solid mask
 // Cell kind bits and, for cells that use the store-side bounce-back convention (F_REDIR: interior
@@ -91,16 +99,18 @@ template <int S, bool FORCE>
 LBM_HD void cell_local(const StepArgs &a, int n) {
     using Cd = Codec<S>;
     using T = typename Cd::T;
-    const uint8_t fl = a.flags[n];
-    if (fl & F_SOLID) return;
     T *const *P = (T *const *)a.plane;
     float g[Q];
+    // the loads do not wait for the flag byte (values of solid / equilibrium cells are unused)
+    static_assert(S == LBM_F32, "16-bit storage updates cells in pairs");
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = ld_early_f32((const float *)P[i] + n);
+    const uint8_t fl = a.flags[n];
+    if (fl & F_SOLID) return;
     if (fl & F_EQ) {
         const int z = (int)(n / a.g.sz);
         equilibrium_shifted(a.rho_b - 1.0f, a.ub[3 * z], a.ub[3 * z + 1], a.ub[3 * z + 2], g);
     } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = Cd::dec(P[i][n]);
         collide<FORCE>(g, a);
     }
     if (fl & F_REDIR) {
@@ -127,13 +137,18 @@ LBM_HD void cell_local(const StepArgs &a, int n) {
 // population heading into a solid goes to the cell's own reversed slot.  No load depends on
 // another load.
 template <int S, bool FORCE>
-LBM_HD void cell_neighbor_interior(const StepArgs &a, int n, uint8_t fl) {
+LBM_HD void cell_neighbor_interior(const StepArgs &a, int n) {
     using Cd = Codec<S>;
     using T = typename Cd::T;
     T *const *P = (T *const *)a.plane;
     float g[Q];
+    // the loads do not wait for the flag byte; for a solid or face cell they may fall outside its
+    // neighbourhood but stay inside the workspace (guard after the planes), and are discarded
+    static_assert(S == LBM_F32, "16-bit storage updates cells in pairs");
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = Cd::dec(P[opp(i)][n - a.off[i]]);
+    for (int i = 0; i < Q; ++i) g[i] = ld_early_f32((const float *)P[opp(i)] + n - a.off[i]);
+    const uint8_t fl = a.flags[n];
+    if (fl & (F_SOLID | F_FACE)) return;
     const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
     collide<FORCE>(g, a);
     if (nb) {
@@ -231,6 +246,208 @@ LBM_HD void cell_neighbor_face(const StepArgs &a, uint8_t fl, int x, int y, int 
             T *base = kind == 0 ? f : (T *)a.side[kind - 1];
             base[idx] = v;
         });
+    }
+}
+
+// ---------------------------------------------------------------- two cells per thread (16-bit)
+// With 2-byte populations one cell per thread leaves too few bytes in flight; a thread updates
+// the cells n0 and n1 = n0 + 256 (so every warp access stays 32 consecutive cells), issuing the
+// loads of both before either collision and keeping the two 16-bit values of each direction in one
+// register.  v0 / v1: the cell exists and takes this path.
+
+template <int S, bool FORCE>
+LBM_HD void store_local_one(const StepArgs &a, int n, uint8_t fl, const float (&g)[Q]) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    T *const *P = (T *const *)a.plane;
+    if (fl & F_REDIR) {
+        const unsigned nb = a.info[n] >> 8;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const bool bb = (nb >> i) & 1u;
+            (bb ? P[i] : P[opp(i)])[bb ? n + a.off[i] : n] = Cd::enc(g[i]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) P[opp(i)][n] = Cd::enc(g[i]);
+    }
+    if (fl & F_ZG) {
+        int x, y, z;
+        cell_coords(a.g, n, x, y, z);
+        store_side<T>(a.g, a.side, x, y, z, g, [](float v) { return Cd::enc(v); });
+    }
+}
+
+template <int S, bool FORCE>
+LBM_HD void cell2_local(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
+    using Cd = Codec<S>;
+    const unsigned short *const *P = (const unsigned short *const *)a.plane;
+    uint32_t pk[Q];   // loaded before the flags are known (n1 may be past N: guard region)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) pk[i] = ld_early_u16(P[i] + n0) | (ld_early_u16(P[i] + n1) << 16);
+    const uint8_t f0 = v0 ? a.flags[n0] : F_SOLID, f1 = v1 ? a.flags[n1] : F_SOLID;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const uint8_t fl = c ? f1 : f0;
+        if (fl & F_SOLID) continue;
+        const int n = c ? n1 : n0;
+        float g[Q];
+        if (fl & F_EQ) {
+            const int z = (int)(n / a.g.sz);
+            equilibrium_shifted(a.rho_b - 1.0f, a.ub[3 * z], a.ub[3 * z + 1], a.ub[3 * z + 2], g);
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) g[i] = Cd::dec_bits(c ? pk[i] >> 16 : pk[i] & 0xffffu);
+            collide<FORCE, kPairs16>(g, a);
+        }
+        store_local_one<S, FORCE>(a, n, fl, g);
+    }
+}
+
+template <int S, bool FORCE>
+LBM_HD void cell2_neighbor_interior(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
+    using Cd = Codec<S>;
+    unsigned short *const *P = (unsigned short *const *)a.plane;
+    uint32_t pk[Q];   // loaded before the flags are known (guard region after the planes)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const unsigned short *p = P[opp(i)] - a.off[i];
+        pk[i] = ld_early_u16(p + n0) | (ld_early_u16(p + n1) << 16);
+    }
+    const uint8_t f0 = v0 ? a.flags[n0] : F_SOLID, f1 = v1 ? a.flags[n1] : F_SOLID;
+    const bool l0 = !(f0 & (F_SOLID | F_FACE)), l1 = !(f1 & (F_SOLID | F_FACE));
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!(c ? l1 : l0)) continue;
+        const int n = c ? n1 : n0;
+        const uint8_t fl = c ? f1 : f0;
+        float g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = Cd::dec_bits(c ? pk[i] >> 16 : pk[i] & 0xffffu);
+        collide<FORCE, kPairs16>(g, a);
+        const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
+        if (nb) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const bool bb = (nb >> i) & 1u;
+                (bb ? P[opp(i)] : P[i])[bb ? n : n + a.off[i]] = Cd::enc_bits(g[i]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) P[i][n + a.off[i]] = Cd::enc_bits(g[i]);
+        }
+    }
+}
+
+// Adjacent pairs (n0 = 2m, n0 + 1) with 4-byte accesses, for 16-bit storage when N and nx are
+// even (plane bases and every c_x = 0 neighbour offset are then 4-byte aligned).  A warp load is
+// 128 bytes, as in FP32 storage.  Pairs whose cells need individual handling (a solid cell, whose
+// slots may be receiving a neighbour's bounce-back store, or a cell with redirected links) fall
+// back to per-cell stores.
+
+template <int S, bool FORCE>
+LBM_HD void cellp_local(const StepArgs &a, int n0) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    const int m = n0 >> 1;
+    uint32_t pk[Q];   // inputs; each half is replaced by its cell's encoded result once computed
+#pragma unroll
+    for (int i = 0; i < Q; ++i) pk[i] = ld_early_u32((const uint32_t *)a.plane[i] + m);   // before the flags
+    const uint8_t f0 = a.flags[n0], f1 = a.flags[n0 + 1];
+    if ((f0 & f1) & F_SOLID) return;
+    // phase 1: both collisions, results packed into pk
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const uint8_t fl = c ? f1 : f0;
+        if (fl & F_SOLID) continue;
+        float g[Q];
+        if (fl & F_EQ) {
+            const int z = (int)((n0 + c) / a.g.sz);
+            equilibrium_shifted(a.rho_b - 1.0f, a.ub[3 * z], a.ub[3 * z + 1], a.ub[3 * z + 2], g);
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) g[i] = Cd::dec_bits(c ? pk[i] >> 16 : pk[i] & 0xffffu);
+            collide<FORCE, kPairs16>(g, a);
+        }
+        if (fl & F_ZG) {
+            int x, y, z;
+            cell_coords(a.g, n0 + c, x, y, z);
+            store_side<T>(a.g, a.side, x, y, z, g, [](float v) { return Cd::enc(v); });
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const uint32_t bits = Cd::enc_bits(g[i]);
+            pk[i] = c ? ((pk[i] & 0xffffu) | (bits << 16)) : ((pk[i] & 0xffff0000u) | bits);
+        }
+    }
+    // phase 2: stores -- one 4-byte store per plane, unless a cell of the pair is solid (its
+    // slots may be receiving a neighbour's bounce-back store) or redirects links
+    if (!((f0 | f1) & (F_SOLID | F_REDIR))) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) ((uint32_t *)a.plane[opp(i)])[m] = pk[i];
+        return;
+    }
+    unsigned short *const *P = (unsigned short *const *)a.plane;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const uint8_t fl = c ? f1 : f0;
+        if (fl & F_SOLID) continue;
+        const int n = n0 + c;
+        const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const bool bb = (nb >> i) & 1u;
+            (bb ? P[i] : P[opp(i)])[bb ? n + a.off[i] : n] = (unsigned short)(c ? pk[i] >> 16 : pk[i] & 0xffffu);
+        }
+    }
+}
+
+template <int S, bool FORCE>
+LBM_HD void cellp_neighbor_interior(const StepArgs &a, int n0) {
+    using Cd = Codec<S>;
+    unsigned short *const *P = (unsigned short *const *)a.plane;
+    const int n1 = n0 + 1;
+    uint32_t pk[Q];   // loaded before the flags are known (guard region after the planes)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const unsigned short *p = P[opp(i)] - a.off[i];
+        if (cx(i) == 0) pk[i] = ld_early_u32((const uint32_t *)(p + n0));   // adjacent, 4-byte aligned
+        else pk[i] = ld_early_u16(p + n0) | (ld_early_u16(p + n1) << 16);
+    }
+    const uint8_t f0 = a.flags[n0], f1 = a.flags[n1];
+    const bool l0 = !(f0 & (F_SOLID | F_FACE)), l1 = !(f1 & (F_SOLID | F_FACE));
+    if (!l0 && !l1) return;
+    // phase 1: both collisions, results packed into pk
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!(c ? l1 : l0)) continue;
+        float g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = Cd::dec_bits(c ? pk[i] >> 16 : pk[i] & 0xffffu);
+        collide<FORCE, kPairs16>(g, a);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const uint32_t bits = Cd::enc_bits(g[i]);
+            pk[i] = c ? ((pk[i] & 0xffffu) | (bits << 16)) : ((pk[i] & 0xffff0000u) | bits);
+        }
+    }
+    // phase 2: stores; the c_x = 0 targets of a plain pair are adjacent and 4-byte aligned
+    const bool plain = l0 && l1 && !((f0 | f1) & F_REDIR);
+    const unsigned nb0 = (l0 && (f0 & F_REDIR)) ? a.info[n0] >> 8 : 0u;
+    const unsigned nb1 = (l1 && (f1 & F_REDIR)) ? a.info[n1] >> 8 : 0u;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (plain && cx(i) == 0) {
+            *(uint32_t *)(P[i] + n0 + a.off[i]) = pk[i];
+            continue;
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (!(c ? l1 : l0)) continue;
+            const int n = c ? n1 : n0;
+            const bool bb = ((c ? nb1 : nb0) >> i) & 1u;
+            (bb ? P[opp(i)] : P[i])[bb ? n : n + a.off[i]] = (unsigned short)(c ? pk[i] >> 16 : pk[i] & 0xffffu);
+        }
     }
 }
 

@@ -107,12 +107,50 @@ template <> struct Codec<LBM_F16S> {
     static constexpr float kScale = 16384.0f;          // 2^14: keeps |g| ~ 1e-9 .. 4 normal
     static LBM_HD float dec(T v) { return __half2float(v) * (1.0f / kScale); }
     static LBM_HD T enc(float g) { return __float2half_rn(g * kScale); }
+    static LBM_HD float dec_bits(unsigned b) { return dec(__ushort_as_half((unsigned short)b)); }
+    static LBM_HD unsigned short enc_bits(float g) { return __half_as_ushort(enc(g)); }
 };
 template <> struct Codec<LBM_BF16S> {
     using T = __nv_bfloat16;
     static LBM_HD float dec(T v) { return __bfloat162float(v); }
     static LBM_HD T enc(float g) { return __float2bfloat16_rn(g); }
+    static LBM_HD float dec_bits(unsigned b) { return dec(__ushort_as_bfloat16((unsigned short)b)); }
+    static LBM_HD unsigned short enc_bits(float g) { return __bfloat16_as_ushort(enc(g)); }
 };
+
+// ---------------------------------------------------------------- early loads
+// Population loads that must be issued before the cell's flag byte is examined (so that the
+// flag load and the population loads overlap instead of costing two DRAM latencies).  Written as
+// volatile PTX so the compiler cannot move them into the branch that uses them.  The addresses
+// may belong to a neighbouring plane or the workspace guard when the cell turns out to be solid or
+// on a face; such values are discarded.  (Host builds read through volatile for the same reason.)
+LBM_HD float ld_early_f32(const float *p) {
+#ifdef __CUDA_ARCH__
+    float v;
+    asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+#else
+    return *(const volatile float *)p;
+#endif
+}
+LBM_HD unsigned ld_early_u16(const unsigned short *p) {
+#ifdef __CUDA_ARCH__
+    unsigned short v;
+    asm volatile("ld.global.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+#else
+    return *(const volatile unsigned short *)p;
+#endif
+}
+LBM_HD uint32_t ld_early_u32(const uint32_t *p) {
+#ifdef __CUDA_ARCH__
+    uint32_t v;
+    asm volatile("ld.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+#else
+    return *(const volatile uint32_t *)p;
+#endif
+}
 
 // ---------------------------------------------------------------- kernel arguments
 struct Geo {
@@ -140,6 +178,8 @@ struct StepArgs {
     int zwrap;                  // nz * sz: cell offset of a periodic wrap along z
     long long zface_begin;      // first face-enumeration index of the z faces (interior x, y)
     int zfast;                  // bit 0 / bit 1: the z- / z+ face cells take the layer path
+    int pack16;                 // 16-bit storage with N and nx even: lattice blocks update pairs of
+                                // adjacent cells with 4-byte accesses
 };
 
 // The z face layers whose cells (with interior x and y) take the layer path: no-slip or free-slip
@@ -166,8 +206,70 @@ LBM_HD void equilibrium_shifted(float drho, float ux, float uy, float uz,
 
 // Moments (D.1), equilibrium (D.4), non-equilibrium flux (D.8), Q (D.10), tau_eff (D.11),
 // BGK relaxation (D.2), optional Guo source.  g: shifted pre-collision populations in/out.
-template <bool FORCE>
+//
+// Two equivalent evaluation orders (chosen per storage kind by measurement on B300): direction by
+// direction, or -- PAIRS, unforced only -- on opposite pairs (2k-1, 2k): s = g_i + g_opp(i) carries the even
+// moments, d = g_i - g_opp(i) the odd ones, and the equilibrium of a pair splits into a shared
+// even part w (drho + rho (4.5 (c.u)^2 - 1.5 u.u)) and an odd part +-3 w rho c.u, with the
+// per-weight coefficients shared by the members of a pair.  Same arithmetic as D.2 / D.4, about
+// half the operations of evaluating the 19 equilibria one by one.
+template <bool FORCE, bool PAIRS = false>
 LBM_HD void collide(float (&g)[Q], const StepArgs &a) {
+    if (!FORCE && PAIRS) {
+        const float s1 = g[1] + g[2], d1 = g[1] - g[2];        // x
+        const float s3 = g[3] + g[4], d3 = g[3] - g[4];        // y
+        const float s5 = g[5] + g[6], d5 = g[5] - g[6];        // z
+        const float s7 = g[7] + g[8], d7 = g[7] - g[8];        // +x+y
+        const float s9 = g[9] + g[10], d9 = g[9] - g[10];      // +x+z
+        const float s11 = g[11] + g[12], d11 = g[11] - g[12];  // +y+z
+        const float s13 = g[13] + g[14], d13 = g[13] - g[14];  // +x-y
+        const float s15 = g[15] + g[16], d15 = g[15] - g[16];  // +x-z
+        const float s17 = g[17] + g[18], d17 = g[17] - g[18];  // +y-z
+        const float drho = g[0] + (s1 + s3 + s5) + ((s7 + s9) + (s11 + s13)) + (s15 + s17);
+        const float jx = d1 + d7 + d9 + d13 + d15;
+        const float jy = d3 + d7 + d11 - d13 + d17;
+        const float jz = d5 + d9 + d11 - d15 - d17;
+        const float sxx = s1 + s7 + s9 + s13 + s15;
+        const float syy = s3 + s7 + s11 + s13 + s17;
+        const float szz = s5 + s9 + s11 + s15 + s17;
+        const float sxy = s7 - s13, sxz = s9 - s15, syz = s11 - s17;
+        const float rho = 1.0f + drho;
+        const float irho = 1.0f / rho;
+        const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
+        const float d3r = drho * (1.0f / 3.0f);
+        const float pxx = sxx - d3r - jx * ux, pyy = syy - d3r - jy * uy, pzz = szz - d3r - jz * uz;
+        const float pxy = sxy - jx * uy, pxz = sxz - jx * uz, pyz = syz - jy * uz;
+        const float pp = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (pxy * pxy + pxz * pxz + pyz * pyz);
+        const float qn = sqrtf(2.0f * pp);
+        const float tau_e = 0.5f * (a.tau + sqrtf(a.tau * a.tau + a.c2x18 * qn * irho));
+        const float om = 1.0f / tau_e;
+        // per weight class w: even part  w (drho - 1.5 rho u.u) + w 4.5 rho (c.u)^2,
+        //                     odd part   w 3 rho (c.u);   g* = g + om (g^eq - g)
+        const float e = drho - 1.5f * rho * (ux * ux + uy * uy + uz * uz);
+        const float e0 = (1.0f / 3.0f) * e;
+        const float e1 = (1.0f / 18.0f) * e, q1 = 0.25f * rho, a1 = rho * (1.0f / 6.0f);
+        const float e2 = (1.0f / 36.0f) * e, q2 = 0.125f * rho, a2 = rho * (1.0f / 12.0f);
+        g[0] = fmaf(om, e0 - g[0], g[0]);
+#define LBM_PAIR(I, CU, E, Qc, Ac)                              \
+        {                                                        \
+            const float cu_ = (CU);                              \
+            const float sym_ = fmaf(Qc * cu_, cu_, E);           \
+            const float asym_ = Ac * cu_;                        \
+            g[I] = fmaf(om, (sym_ + asym_) - g[I], g[I]);        \
+            g[I + 1] = fmaf(om, (sym_ - asym_) - g[I + 1], g[I + 1]); \
+        }
+        LBM_PAIR(1, ux, e1, q1, a1)
+        LBM_PAIR(3, uy, e1, q1, a1)
+        LBM_PAIR(5, uz, e1, q1, a1)
+        LBM_PAIR(7, ux + uy, e2, q2, a2)
+        LBM_PAIR(9, ux + uz, e2, q2, a2)
+        LBM_PAIR(11, uy + uz, e2, q2, a2)
+        LBM_PAIR(13, ux - uy, e2, q2, a2)
+        LBM_PAIR(15, ux - uz, e2, q2, a2)
+        LBM_PAIR(17, uy - uz, e2, q2, a2)
+#undef LBM_PAIR
+        return;
+    }
     float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
     float sxx = 0.0f, syy = 0.0f, szz = 0.0f, sxy = 0.0f, sxz = 0.0f, syz = 0.0f;
 #pragma unroll
@@ -203,15 +305,14 @@ LBM_HD void collide(float (&g)[Q], const StepArgs &a) {
     equilibrium_shifted(drho, ux, uy, uz, geq);
 #pragma unroll
     for (int i = 0; i < Q; ++i) g[i] = fmaf(om, geq[i] - g[i], g[i]);
-    if (FORCE) {
-        const float pre = 1.0f - 0.5f * om;
-        const float uf = ux * a.fx + uy * a.fy + uz * a.fz;
+    if (!FORCE) return;
+    const float pre = 1.0f - 0.5f * om;
+    const float uf = ux * a.fx + uy * a.fy + uz * a.fz;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-            const float cf = cx(i) * a.fx + cy(i) * a.fy + cz(i) * a.fz;
-            g[i] += pre * wgt(i) * (3.0f * (cf - uf) + 9.0f * cu * cf);
-        }
+    for (int i = 0; i < Q; ++i) {
+        const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+        const float cf = cx(i) * a.fx + cy(i) * a.fy + cz(i) * a.fz;
+        g[i] += pre * wgt(i) * (3.0f * (cf - uf) + 9.0f * cu * cf);
     }
 }
 
