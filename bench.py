@@ -163,6 +163,12 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def weak_scaling_glups(cells: int, steps: int, world: int, slowest_ms: float) -> float:
+    """Whole-job throughput of ``world`` independent replicas: every rank updated ``cells`` cells
+    ``steps`` times; the job took as long as its slowest rank."""
+    return cells * steps * world / (slowest_ms / 1e3) / 1e9
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -291,7 +297,7 @@ def run_ours(args, rank, world):
                                                 clock_id if rank == 0 else None)
     total_ms = max_over_ranks(total_ms, world)
     diag = dom.diagnostics()
-    value = N * args.steps * world / (total_ms / 1e3) / 1e9
+    value = weak_scaling_glups(N, args.steps, world, total_ms)
 
     sb = STORE_BYTES[args.store]
     alg_bytes = nonsolid * 2 * 19 * sb + N            # read + write every population, + flags
@@ -317,7 +323,7 @@ def run_ours(args, rank, world):
         t_ms, nb2, lc2, _, _ = time_steps(d2, max(200, args.steps // 4), min(args.warmup, 200), world, None)
         t_ms = max_over_ranks(t_ms, world)
         K2 = max(200, args.steps // 4)
-        g2 = N * K2 * world / (t_ms / 1e3) / 1e9
+        g2 = weak_scaling_glups(N, K2, world, t_ms)
         ab2 = nonsolid * 2 * 19 * STORE_BYTES[st] + N
         avg2 = max(sum(nb2) / len(nb2), sum(lc2) / len(lc2))
         variants[st] = {"glups": g2, "vs_f32": g2 / value if args.store == "f32" else None,
