@@ -10,7 +10,7 @@ written with tensor contractions over the whole lattice.
 
 Same paper passages as the C oracle: App. D (D.1 moments, D.2 BGK, D.3 streaming, D.4
 equilibrium, D.8-D.11 Smagorinsky closure, mid-grid bounce-back), Sec. 3 (equilibrium velocity
-faces), Guo forcing (named in App. E).  Same readings where the paper is silent.
+faces), Guo forcing and the Coriolis force (App. E).  Same readings where the paper is silent.
 
 Only for small lattices (a few thousand cells): it materialises several padded copies.
 """
@@ -90,7 +90,7 @@ def _pad(P: np.ndarray, wall: np.ndarray, axis_pop: int, a: int, lo: str, hi: st
 
 
 def step(F: np.ndarray, kind: np.ndarray, faces, ub: np.ndarray, tau: float, Cs: float,
-         force=None, rho_b: float = 1.0) -> np.ndarray:
+         force=None, rho_b: float = 1.0, omega=None) -> np.ndarray:
     """One step.  F (19, nz, ny, nx) in THIS module's direction order."""
     nz, ny, nx = kind.shape
     wall = kind == SOLID
@@ -106,7 +106,7 @@ def step(F: np.ndarray, kind: np.ndarray, faces, ub: np.ndarray, tau: float, Cs:
     # collision over the whole lattice (solid cells produce junk here and are overwritten below)
     Fv = np.zeros(3) if force is None else np.asarray(force, np.float64)
     with np.errstate(divide="ignore", invalid="ignore"):
-        out = _collide(f, Fv, tau, Cs)
+        out = _collide(f, Fv, tau, Cs, omega)
     # boundary cells
     Z = np.broadcast_to(np.arange(nz)[:, None, None], kind.shape)
     feq_b = equilibrium(np.full(kind.shape, rho_b), np.asarray(ub)[Z])
@@ -115,16 +115,20 @@ def step(F: np.ndarray, kind: np.ndarray, faces, ub: np.ndarray, tau: float, Cs:
     return out
 
 
-def _collide(f: np.ndarray, Fv: np.ndarray, tau: float, Cs: float) -> np.ndarray:
+def _collide(f: np.ndarray, Fv: np.ndarray, tau: float, Cs: float, omega=None) -> np.ndarray:
     rho = f.sum(axis=0)
     mom = np.einsum("qa,q...->...a", C.astype(np.float64), f)
-    u = (mom + 0.5 * Fv) / rho[..., None]
+    # body force per cell: uniform part + Coriolis rho 2 Omega x (mom / rho)  (App. E)
+    Fc = np.broadcast_to(Fv, mom.shape).copy()
+    if omega is not None:
+        Fc = Fc + 2.0 * np.cross(np.asarray(omega, np.float64), mom)
+    u = (mom + 0.5 * Fc) / rho[..., None]
     feq = equilibrium(rho, u)
     Pi = np.einsum("qa,qb,q...->...ab", C.astype(np.float64), C.astype(np.float64), f - feq)
     Q = np.sqrt(2.0 * np.einsum("...ab,...ab->...", Pi, Pi))
     te = 0.5 * (tau + np.sqrt(tau ** 2 + 2.0 * Cs ** 2 * Q / (rho * CS2 ** 2)))
-    cF = np.einsum("qa,a->q", C.astype(np.float64), Fv).reshape(19, 1, 1, 1)
-    uF = np.einsum("...a,a->...", u, Fv)
+    cF = np.einsum("qa,...a->q...", C.astype(np.float64), Fc)
+    uF = np.einsum("...a,...a->...", u, Fc)
     cu = np.einsum("qa,...a->q...", C.astype(np.float64), u)
     S = (1.0 - 0.5 / te) * W.reshape(19, 1, 1, 1) * ((cF - uF) / CS2 + cu * cF / CS2 ** 2)
     return f - (f - feq) / te + S

@@ -16,8 +16,8 @@
  *   - streaming f_i(x + c_i, t + 1) = f*_i(x, t)                                   (D.3)
  *   - halfway (mid-grid) bounce-back at solid cells and no-slip faces  (App. D, last paragraph)
  *   - equilibrium velocity boundary cells (Sec. 3, boundary-condition paragraph)
- *   - optional uniform body force by Guo's forcing (App. E names the method; used here only for
- *     the laminar channel check)
+ *   - optional uniform body force and Coriolis force F_c = rho 2 Omega x u (App. E), both applied
+ *     by Guo's forcing scheme
  *
  * The step is written as a two-lattice PULL: Fout(x) is computed from Fin (the post-collision
  * state of the previous step) by gathering each population from its upstream neighbour and then
@@ -118,10 +118,13 @@ double oracle_tau_eff(double tau, double C, double Q, double rho)
 
 /* ---- one cell: moments, equilibrium, LES closure, BGK (+ Guo source) ----
  * f:     pre-collision populations (post-stream)
- * force: body-force density (may be NULL)
+ * force: uniform body-force density (may be NULL)
+ * omega: rotation vector Omega^lbm of the Coriolis force (may be NULL); App. E: once rho and u
+ *        are recovered from the populations, F_c = rho 2 Omega^lbm x u joins the body force
+ *        that Guo's scheme applies (u here = sum c f / rho, before any force correction)
  * out:   post-collision populations; q_out / tau_out optional diagnostics */
-void oracle_collide(const double f[ORQ], double tau, double C, const double *force, double out[ORQ],
-                    double *q_out, double *tau_out)
+void oracle_collide_rot(const double f[ORQ], double tau, double C, const double *force,
+                        const double *omega, double out[ORQ], double *q_out, double *tau_out)
 {
     tables();
     const double cs2 = 1.0 / 3.0;
@@ -133,6 +136,12 @@ void oracle_collide(const double f[ORQ], double tau, double C, const double *for
     for (int i = 0; i < ORQ; ++i) {
         rho += f[i];
         for (int a = 0; a < 3; ++a) m[a] += oc[i][a] * f[i];
+    }
+    if (omega) { /* App. E: F_c = rho 2 Omega x u with u = m / rho */
+        const double v[3] = {m[0] / rho, m[1] / rho, m[2] / rho};
+        F[0] += rho * 2.0 * (omega[1] * v[2] - omega[2] * v[1]);
+        F[1] += rho * 2.0 * (omega[2] * v[0] - omega[0] * v[2]);
+        F[2] += rho * 2.0 * (omega[0] * v[1] - omega[1] * v[0]);
     }
     /* Guo: the velocity carries half the force impulse */
     double u[3];
@@ -167,6 +176,12 @@ void oracle_collide(const double f[ORQ], double tau, double C, const double *for
     }
     if (q_out) *q_out = Q;
     if (tau_out) *tau_out = te;
+}
+
+void oracle_collide(const double f[ORQ], double tau, double C, const double *force, double out[ORQ],
+                    double *q_out, double *tau_out)
+{
+    oracle_collide_rot(f, tau, C, force, NULL, out, q_out, tau_out);
 }
 
 /* ---- cell classification: solid mask wins, then equilibrium-face layers, else fluid ---- */
@@ -281,10 +296,12 @@ static double gather(const double *Fin, const uint8_t *kind, const int n[3], siz
 /* ---- one full time step over z-planes [z0, z1) (pass 0, nz for the whole lattice) ----
  * Fin:  post-collision state at step t (19 x N, population-major, x fastest)
  * Fout: post-collision state at step t+1
- * q_out, tau_out: optional per-cell Q and tau_eff of the step (fluid cells; NaN elsewhere) */
+ * q_out, tau_out: optional per-cell Q and tau_eff of the step (fluid cells; NaN elsewhere)
+ * omega: optional Coriolis rotation vector (lattice units) */
 int oracle_step(const double *Fin, double *Fout, const uint8_t *kind, int nx, int ny, int nz,
                 const int face[6], const double *ub, double rho_b, double tau, double C,
-                const double *force, int z0, int z1, double *q_out, double *tau_out)
+                const double *force, int z0, int z1, double *q_out, double *tau_out,
+                const double *omega)
 {
     tables();
     const int n[3] = {nx, ny, nz};
@@ -305,7 +322,7 @@ int oracle_step(const double *Fin, double *Fout, const uint8_t *kind, int nx, in
                 } else {
                     const int p[3] = {x, y, z};
                     for (int i = 0; i < ORQ; ++i) f[i] = gather(Fin, kind, n, N, face, p, i);
-                    oracle_collide(f, tau, C, force, out, &q, &te);
+                    oracle_collide_rot(f, tau, C, force, omega, out, &q, &te);
                 }
                 for (int i = 0; i < ORQ; ++i) Fout[(size_t)i * N + c] = out[i];
                 if (q_out) q_out[c] = q;

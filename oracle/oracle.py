@@ -62,13 +62,15 @@ def lib() -> ctypes.CDLL:
         L.oracle_tau_eff.restype = D
         L.oracle_collide.argtypes = [P, D, D, P, P, P, P]
         L.oracle_collide.restype = None
+        L.oracle_collide_rot.argtypes = [P, D, D, P, P, P, P, P]
+        L.oracle_collide_rot.restype = None
         L.oracle_classify.argtypes = [P, I, I, I, P, P]
         L.oracle_classify.restype = I
         L.oracle_expand_profile.argtypes = [P, I, I, D, P]
         L.oracle_expand_profile.restype = I
         L.oracle_init.argtypes = [P, P, I, I, I, P, P, P, D]
         L.oracle_init.restype = I
-        L.oracle_step.argtypes = [P, P, P, I, I, I, P, P, D, D, D, P, I, I, P, P]
+        L.oracle_step.argtypes = [P, P, P, I, I, I, P, P, D, D, D, P, I, I, P, P, P]
         L.oracle_step.restype = I
         L.oracle_macros.argtypes = [P, P, I, I, I, P, D, P, P, P]
         L.oracle_macros.restype = I
@@ -106,15 +108,16 @@ def tau_eff(tau: float, C: float, Q: float, rho: float) -> float:
     return lib().oracle_tau_eff(float(tau), float(C), float(Q), float(rho))
 
 
-def collide(f, tau: float, C: float, force=None):
-    """One-cell collision; returns (f*, Q, tau_eff)."""
+def collide(f, tau: float, C: float, force=None, omega=None):
+    """One-cell collision; returns (f*, Q, tau_eff).  ``omega``: Coriolis rotation vector."""
     f = np.ascontiguousarray(f, np.float64)
     out = np.zeros(19, np.float64)
     q = ctypes.c_double()
     te = ctypes.c_double()
     fz = None if force is None else np.ascontiguousarray(force, np.float64)
-    lib().oracle_collide(_p(f), float(tau), float(C), _p(fz), _p(out),
-                         ctypes.addressof(q), ctypes.addressof(te))
+    om = None if omega is None else np.ascontiguousarray(omega, np.float64)
+    lib().oracle_collide_rot(_p(f), float(tau), float(C), _p(fz), _p(om), _p(out),
+                             ctypes.addressof(q), ctypes.addressof(te))
     return out, q.value, te.value
 
 
@@ -148,8 +151,9 @@ def init(kind: np.ndarray, ub: np.ndarray, rho=None, u=None, rho_b: float = 1.0)
 
 def step(F: np.ndarray, kind: np.ndarray, faces, ub: np.ndarray, tau: float, C: float,
          force=None, rho_b: float = 1.0, z0: int = 0, z1: int | None = None,
-         out: np.ndarray | None = None, diag: bool = False):
-    """One time step (pull form).  Returns F_next, or (F_next, Q, tau_eff) if ``diag``."""
+         out: np.ndarray | None = None, diag: bool = False, omega=None):
+    """One time step (pull form).  Returns F_next, or (F_next, Q, tau_eff) if ``diag``.
+    ``omega``: Coriolis rotation vector (lattice units), None = no Coriolis force."""
     nz, ny, nx = kind.shape
     if out is None:
         out = np.zeros_like(F)
@@ -158,9 +162,10 @@ def step(F: np.ndarray, kind: np.ndarray, faces, ub: np.ndarray, tau: float, C: 
     if diag:
         q = np.zeros((nz, ny, nx), np.float64)
         te = np.zeros((nz, ny, nx), np.float64)
+    om = None if omega is None else np.ascontiguousarray(omega, np.float64)
     lib().oracle_step(_p(F), _p(out), _p(kind), nx, ny, nz, _p(_faces(faces)),
                       _p(np.ascontiguousarray(ub, np.float64)), float(rho_b), float(tau), float(C),
-                      _p(fz), int(z0), int(nz if z1 is None else z1), _p(q), _p(te))
+                      _p(fz), int(z0), int(nz if z1 is None else z1), _p(q), _p(te), _p(om))
     return (out, q, te) if diag else out
 
 
