@@ -78,11 +78,19 @@ typedef struct {
     float force[3];       /* uniform body-force density, Guo forcing; {0,0,0} = none */
     int watchdog_every;   /* > 0: lbm_step scans for non-finite populations every that many
                              steps (synchronises the stream); 0 = off */
+    float coriolis[3];    /* rotation vector Omega^lbm (lattice units, e.g. lbm_coriolis_omega);
+                             each fluid cell adds the Coriolis force 2 rho Omega^lbm x u, u = sum c f
+                             / rho, to the body force of Guo's forcing (App. E); {0,0,0} = none */
 } lbm_params;
 
 /* Fill p with defaults: tau 0.52, C 0.16, rho_b 1, F32, x- inflow, x+ outflow, periodic y,
- * no-slip ground, free-slip top, no force, no watchdog.  Returns LBM_EINVAL if p is NULL. */
+ * no-slip ground, free-slip top, no force, no rotation, no watchdog.  Returns LBM_EINVAL if p
+ * is NULL. */
 lbm_status lbm_params_default(lbm_params *p);
+
+/* Earth rotation in the local east-north-up frame at latitude lat_deg, in lattice units (App. E):
+ * Omega^lbm = Omega dt_si (0, cos lat, sin lat) with Omega = 7.292115e-5 rad/s.  out: 3 floats. */
+lbm_status lbm_coriolis_omega(double lat_deg, double dt_si, float *out);
 
 /* Lateral face kinds for a wind direction theta (radians, 0 = +x, counter-clockwise): a lateral
  * face is INFLOW_EQ when the wind enters through it (u . n_in > 1e-6 |u|), OUTFLOW_ZG otherwise;

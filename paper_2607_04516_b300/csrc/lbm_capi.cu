@@ -42,6 +42,8 @@ const char *check_args(int nx, int ny, int nz, const lbm_params *p) {
     if (p->store < LBM_F32 || p->store > LBM_BF16S) return "unknown storage kind";
     for (int k = 0; k < 3; ++k)
         if (!std::isfinite(p->force[k])) return "force must be finite";
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(p->coriolis[k])) return "coriolis must be finite";
     const int n[3] = {nx, ny, nz};
     for (int a = 0; a < 3; ++a) {
         const int lo = p->face[2 * a], hi = p->face[2 * a + 1];
@@ -131,6 +133,7 @@ StepArgs args_of(const lbm_domain *d) {
     a.c2x18 = 18.0f * d->p.cs_smag * d->p.cs_smag;
     a.rho_b = d->p.rho_b;
     a.fx = d->p.force[0]; a.fy = d->p.force[1]; a.fz = d->p.force[2];
+    a.ox = d->p.coriolis[0]; a.oy = d->p.coriolis[1]; a.oz = d->p.coriolis[2];
     a.nface = face_cell_count(a.g);
     const size_t sb = store_bytes(d->p.store);
     for (int i = 0; i < Q; ++i) {
@@ -147,7 +150,9 @@ StepArgs args_of(const lbm_domain *d) {
 }
 
 bool has_force(const lbm_domain *d) {
-    return d->p.force[0] != 0.0f || d->p.force[1] != 0.0f || d->p.force[2] != 0.0f;
+    for (int k = 0; k < 3; ++k)
+        if (d->p.force[k] != 0.0f || d->p.coriolis[k] != 0.0f) return true;
+    return false;
 }
 
 }  // namespace
@@ -171,6 +176,16 @@ lbm_status lbm_params_default(lbm_params *p) {
     const int f[6] = {LBM_FACE_INFLOW_EQ, LBM_FACE_OUTFLOW_ZG, LBM_FACE_PERIODIC,
                       LBM_FACE_PERIODIC, LBM_FACE_NOSLIP, LBM_FACE_FREESLIP};
     for (int k = 0; k < 6; ++k) p->face[k] = f[k];
+    return LBM_OK;
+}
+
+lbm_status lbm_coriolis_omega(double lat_deg, double dt_si, float *out) {
+    if (!out || !std::isfinite(lat_deg) || !std::isfinite(dt_si) || dt_si <= 0.0) return LBM_EINVAL;
+    const double kOmega = 7.292115e-5;   // Earth's rotation rate [rad/s] (App. E)
+    const double lat = lat_deg * 3.14159265358979323846 / 180.0;
+    out[0] = 0.0f;
+    out[1] = (float)(kOmega * dt_si * std::cos(lat));
+    out[2] = (float)(kOmega * dt_si * std::sin(lat));
     return LBM_OK;
 }
 

@@ -171,7 +171,8 @@ struct StepArgs {
     float tau;
     float c2x18;                // 2 (C Delta)^2 / c_s^4 = 18 C^2
     float rho_b;
-    float fx, fy, fz;           // body-force density (Guo)
+    float fx, fy, fz;           // uniform body-force density (Guo)
+    float ox, oy, oz;           // Coriolis rotation vector Omega^lbm (force 2 rho Omega x u)
     long long nface;            // cells on face layers (enumerated by face_cell_xyz)
     void *plane[Q];             // base address of population plane i (= f + i * N elements)
     int off[Q];                 // cell offset of the neighbour x + c_i (c_x + c_y sy + c_z sz)
@@ -287,10 +288,14 @@ LBM_HD void collide(float (&g)[Q], const StepArgs &a) {
     }
     const float rho = 1.0f + drho;
     const float irho = 1.0f / rho;
+    // body force of this cell: uniform part + Coriolis 2 rho Omega x (j / rho) = 2 Omega x j (App. E)
+    const float Fx = FORCE ? a.fx + 2.0f * (a.oy * jz - a.oz * jy) : 0.0f;
+    const float Fy = FORCE ? a.fy + 2.0f * (a.oz * jx - a.ox * jz) : 0.0f;
+    const float Fz = FORCE ? a.fz + 2.0f * (a.ox * jy - a.oy * jx) : 0.0f;
     if (FORCE) {
-        jx += 0.5f * a.fx;
-        jy += 0.5f * a.fy;
-        jz += 0.5f * a.fz;
+        jx += 0.5f * Fx;
+        jy += 0.5f * Fy;
+        jz += 0.5f * Fz;
     }
     const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
     // Pi^neq = sum c c g - drho/3 delta - rho u u   (since sum c c w = delta/3)
@@ -307,11 +312,11 @@ LBM_HD void collide(float (&g)[Q], const StepArgs &a) {
     for (int i = 0; i < Q; ++i) g[i] = fmaf(om, geq[i] - g[i], g[i]);
     if (!FORCE) return;
     const float pre = 1.0f - 0.5f * om;
-    const float uf = ux * a.fx + uy * a.fy + uz * a.fz;
+    const float uf = ux * Fx + uy * Fy + uz * Fz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-        const float cf = cx(i) * a.fx + cy(i) * a.fy + cz(i) * a.fz;
+        const float cf = cx(i) * Fx + cy(i) * Fy + cz(i) * Fz;
         g[i] += pre * wgt(i) * (3.0f * (cf - uf) + 9.0f * cu * cf);
     }
 }

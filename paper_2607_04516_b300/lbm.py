@@ -32,7 +32,7 @@ class LbmError(RuntimeError):
 class lbm_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("cs_smag", ctypes.c_float), ("rho_b", ctypes.c_float),
                 ("store", ctypes.c_int), ("face", ctypes.c_int * 6), ("force", ctypes.c_float * 3),
-                ("watchdog_every", ctypes.c_int)]
+                ("watchdog_every", ctypes.c_int), ("coriolis", ctypes.c_float * 3)]
 
 
 # exported symbols and their ctypes signatures (the header is the authority)
@@ -41,6 +41,7 @@ _PP = ctypes.POINTER(lbm_params)
 SIGNATURES = {
     "lbm_params_default": (_I, [_PP]),
     "lbm_faces_for_direction": (_I, [_F, _P]),
+    "lbm_coriolis_omega": (_I, [ctypes.c_double, ctypes.c_double, _P]),
     "lbm_workspace_bytes": (_SZ, [_I, _I, _I, _PP]),
     "lbm_create_domain": (_I, [_P, _I, _I, _I, _PP, _P, _SZ, _P, ctypes.POINTER(_P)]),
     "lbm_set_stream": (_I, [_P, _P]),
@@ -97,7 +98,8 @@ def _check(status: int, dom=None):
         raise LbmError(status, msg)
 
 
-def make_params(faces, tau=0.52, cs=0.16, store="f32", rho_b=1.0, force=None, watchdog_every=0):
+def make_params(faces, tau=0.52, cs=0.16, store="f32", rho_b=1.0, force=None, watchdog_every=0,
+                coriolis=None):
     p = lbm_params()
     load(False).lbm_params_default(ctypes.byref(p))
     p.tau = tau
@@ -109,6 +111,8 @@ def make_params(faces, tau=0.52, cs=0.16, store="f32", rho_b=1.0, force=None, wa
     for k in range(3):
         p.force[k] = 0.0 if force is None else float(force[k])
     p.watchdog_every = watchdog_every
+    for k in range(3):
+        p.coriolis[k] = 0.0 if coriolis is None else float(coriolis[k])
     return p
 
 
@@ -117,6 +121,12 @@ def lbm_faces_for_direction(theta: float) -> tuple:
     face = (ctypes.c_int * 6)()
     _check(load(False).lbm_faces_for_direction(theta, face))
     return tuple(FACE_NAMES[v] for v in face)
+
+
+def lbm_coriolis_omega(lat_deg: float, dt_si: float):
+    out = (ctypes.c_float * 3)()
+    _check(load(False).lbm_coriolis_omega(float(lat_deg), float(dt_si), out))
+    return tuple(out)
 
 
 def lbm_workspace_bytes(nx: int, ny: int, nz: int, params: lbm_params) -> int:
@@ -193,7 +203,7 @@ class Domain:
 
     def __init__(self, solid: np.ndarray, faces, tau: float = 0.52, cs: float = 0.16,
                  store: str = "f32", rho_b: float = 1.0, force=None, watchdog_every: int = 0,
-                 device: str = "cuda", stream=None):
+                 device: str = "cuda", stream=None, coriolis=None):
         import torch
         load()
         self.shape = tuple(solid.shape)
@@ -201,7 +211,7 @@ class Domain:
         self.N = nx * ny * nz
         self.faces = tuple(faces)
         self.store = store
-        self.params = make_params(faces, tau, cs, store, rho_b, force, watchdog_every)
+        self.params = make_params(faces, tau, cs, store, rho_b, force, watchdog_every, coriolis)
         nbytes = lbm_workspace_bytes(nx, ny, nz, self.params)
         if nbytes == 0:
             raise LbmError(-1, "invalid domain arguments")

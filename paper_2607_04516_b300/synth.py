@@ -35,6 +35,7 @@ class Case:
     u0: np.ndarray | None = None      # (nz, ny, nx, 3) initial velocity (None: profile)
     rho0: np.ndarray | None = None    # (nz, ny, nx) initial density (None: 1)
     force: tuple | None = None        # uniform body-force density (Guo forcing), lattice units
+    coriolis: tuple | None = None     # rotation vector Omega^lbm of the Coriolis force, lattice units
     rho_b: float = 1.0
     meta: dict = field(default_factory=dict)
 

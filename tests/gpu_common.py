@@ -28,7 +28,8 @@ def lib_to_oracle_order():
 
 def gpu_domain(case: synth.Case, store: str = "f32", **kw):
     from paper_2607_04516_b300 import lbm
-    dom = lbm.Domain(case.solid, case.faces, case.tau, case.cs, store, case.rho_b, case.force, **kw)
+    dom = lbm.Domain(case.solid, case.faces, case.tau, case.cs, store, case.rho_b, case.force,
+                     coriolis=case.coriolis, **kw)
     dom.set_inflow_profile(f32(case.speed), case.theta)
     dom.init_fields(f32(case.rho0), f32(case.u0))
     return dom
@@ -54,9 +55,11 @@ def oracle_inputs(case: synth.Case):
 def oracle_run(case: synth.Case, nsteps: int):
     kind, ub = oracle_inputs(case)
     F = orc.init(kind, ub, f64_of_f32(case.rho0), f64_of_f32(case.u0), case.rho_b)
-    F = orc.run(F, nsteps, kind, case.faces, ub, case.tau, case.cs, force=case.force,
-                rho_b=case.rho_b)
-    rho, u = orc.macros(F, kind, ub, case.rho_b, case.force)
+    om = None if case.coriolis is None else f64_of_f32(case.coriolis)
+    fz = None if case.force is None else f64_of_f32(case.force)
+    F = orc.run(F, nsteps, kind, case.faces, ub, case.tau, case.cs, force=fz,
+                rho_b=case.rho_b, omega=om)
+    rho, u = orc.macros(F, kind, ub, case.rho_b, fz)
     return rho, u, F, kind, ub
 
 

@@ -131,3 +131,22 @@ def test_binding_refuses_to_run_without_a_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         lbm.Domain(np.zeros((4, 4, 4), np.uint8), ("periodic",) * 6)
+
+
+def test_coriolis_omega_is_earth_rotation_in_the_local_enu_frame(lib):
+    """App. E: Omega_ENU = Omega (0, cos lat, sin lat), Omega = 7.292115e-5 rad/s, times dt."""
+    lat, dt = 23.113, 0.01
+    om = lbm.lbm_coriolis_omega(lat, dt)
+    w = 7.292115e-5 * dt
+    assert om[0] == 0.0
+    assert om[1] == pytest.approx(w * math.cos(math.radians(lat)), rel=1e-6)
+    assert om[2] == pytest.approx(w * math.sin(math.radians(lat)), rel=1e-6)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_coriolis_omega(10.0, -1.0)
+
+
+def test_params_default_has_no_rotation(lib):
+    p = lbm.make_params(("periodic",) * 6)
+    assert tuple(p.coriolis) == (0.0, 0.0, 0.0)
+    assert lbm.lbm_workspace_bytes(8, 8, 8, lbm.make_params(("periodic",) * 6,
+                                                            coriolis=(0, 0, float("nan")))) == 0

@@ -255,3 +255,34 @@ def test_runs_on_a_side_stream():
     s.synchronize()
     rho2, u2, _ = gpu_run(case, 20, "f32")
     np.testing.assert_array_equal(u.cpu().numpy(), u2.astype(np.float32))
+
+
+# ------------------------------------------------------------------ Coriolis force (App. E)
+@pytest.mark.parametrize("faces", FACE_SETS[:3] + [FACE_SETS[6]])
+@pytest.mark.parametrize("nsteps", [1, 4])
+def test_small_lattices_with_coriolis_populations(faces, nsteps):
+    case = synth.random_small_case(13, 7, 6, faces, seed=21, solid_fraction=0.12, margin=0)
+    case.coriolis = (1e-3, -2e-3, 3e-3)
+    case.force = (1e-5, 0.0, -2e-5)
+    dom = gpu_domain(case, "f32")
+    dom.step(nsteps)
+    g = dom.export_populations().cpu().numpy()
+    _, _, F, kind, _ = oracle_run(case, nsteps)
+    _, wo, _ = orc.lattice()
+    G = g[lib_to_oracle_order()] + wo[:, None, None, None]
+    diff = np.abs(G - F)[:, kind != orc.SOLID]
+    assert diff.max() <= 2e-6, diff.max()
+
+
+@pytest.mark.parametrize("store", ["f32", "f16s"])
+def test_cube_with_coriolis(store):
+    """The cube flow with an exaggerated rotation (|Omega^lbm| ~ 1e-3, a thousand times Earth's at a
+    5 m / 0.01 s lattice) so that the force changes the field visibly within 200 steps."""
+    case = synth.cube_case()
+    case.coriolis = (0.0, 6e-4, 8e-4)
+    rho, u, _ = gpu_run(case, 200, store)
+    rr, ur, _, kind, _ = _oracle_cached(("cube-rot", 200), case, 200)
+    ref0 = _oracle_cached(("cube", 200), synth.cube_case(), 200)[1]
+    fl = kind == orc.FLUID
+    assert rel_l2(ur, ref0, fl) > 10 * TOL_U[store]          # the rotation matters here
+    assert rel_l2(u, ur, fl) <= TOL_U[store]
