@@ -18,6 +18,8 @@
  *   - equilibrium velocity boundary cells (Sec. 3, boundary-condition paragraph)
  *   - optional uniform body force and Coriolis force F_c = rho 2 Omega x u (App. E), both applied
  *     by Guo's forcing scheme
+ *   - synthetic von Karman inflow turbulence on the equilibrium boundary cells (App. F), by direct
+ *     summation of the Fourier modes (oracle_stg)
  *
  * The step is written as a two-lattice PULL: Fout(x) is computed from Fin (the post-collision
  * state of the previous step) by gathering each population from its upstream neighbour and then
@@ -236,7 +238,7 @@ int oracle_expand_profile(const double *speed, int L, int nz, double theta, doub
 /* ---- initial state: F = f^eq(rho, u) per cell ----
  * rho, u may be NULL (rho = 1, u = u_b(z)).  Equilibrium cells take f^eq(rho_b, u_b(z)); solid 0. */
 int oracle_init(double *F, const uint8_t *kind, int nx, int ny, int nz, const double *rho,
-                const double *u, const double *ub, double rho_b)
+                const double *u, const double *ub, double rho_b, const double *ueq)
 {
     tables();
     const size_t N = (size_t)nx * ny * nz;
@@ -248,7 +250,7 @@ int oracle_init(double *F, const uint8_t *kind, int nx, int ny, int nz, const do
             continue;
         }
         if (kind[c] == OR_EQ) {
-            oracle_equilibrium(rho_b, ub + 3 * z, feq);
+            oracle_equilibrium(rho_b, ueq ? ueq + 3 * c : ub + 3 * z, feq);
         } else {
             double uc[3];
             for (int a = 0; a < 3; ++a) uc[a] = u ? u[3 * c + a] : ub[3 * z + a];
@@ -297,11 +299,12 @@ static double gather(const double *Fin, const uint8_t *kind, const int n[3], siz
  * Fin:  post-collision state at step t (19 x N, population-major, x fastest)
  * Fout: post-collision state at step t+1
  * q_out, tau_out: optional per-cell Q and tau_eff of the step (fluid cells; NaN elsewhere)
- * omega: optional Coriolis rotation vector (lattice units) */
+ * omega: optional Coriolis rotation vector (lattice units)
+ * ueq:   optional per-cell velocity of the equilibrium boundary cells (N x 3); NULL = u_b(z) */
 int oracle_step(const double *Fin, double *Fout, const uint8_t *kind, int nx, int ny, int nz,
                 const int face[6], const double *ub, double rho_b, double tau, double C,
                 const double *force, int z0, int z1, double *q_out, double *tau_out,
-                const double *omega)
+                const double *omega, const double *ueq)
 {
     tables();
     const int n[3] = {nx, ny, nz};
@@ -318,7 +321,7 @@ int oracle_step(const double *Fin, double *Fout, const uint8_t *kind, int nx, in
                 if (kind[c] == OR_SOLID) {
                     for (int i = 0; i < ORQ; ++i) out[i] = 0.0;
                 } else if (kind[c] == OR_EQ) {
-                    oracle_equilibrium(rho_b, ub + 3 * z, out);
+                    oracle_equilibrium(rho_b, ueq ? ueq + 3 * c : ub + 3 * z, out);
                 } else {
                     const int p[3] = {x, y, z};
                     for (int i = 0; i < ORQ; ++i) f[i] = gather(Fin, kind, n, N, face, p, i);
@@ -335,7 +338,7 @@ int oracle_step(const double *Fin, double *Fout, const uint8_t *kind, int nx, in
  * fluid: rho = sum F*, u = (sum c F* - F/2) / rho (Guo: sum c F* = rho u + F/2 after collision)
  * equilibrium cells: (rho_b, u_b(z)); solid: rho = 0, u = 0. */
 int oracle_macros(const double *F, const uint8_t *kind, int nx, int ny, int nz, const double *ub,
-                  double rho_b, const double *force, double *rho, double *u)
+                  double rho_b, const double *force, double *rho, double *u, const double *ueq)
 {
     tables();
     const size_t N = (size_t)nx * ny * nz;
@@ -350,7 +353,7 @@ int oracle_macros(const double *F, const uint8_t *kind, int nx, int ny, int nz, 
         }
         if (kind[c] == OR_EQ) {
             rho[c] = rho_b;
-            for (int a = 0; a < 3; ++a) u[3 * c + a] = ub[3 * z + a];
+            for (int a = 0; a < 3; ++a) u[3 * c + a] = ueq ? ueq[3 * c + a] : ub[3 * z + a];
             continue;
         }
         double r = 0.0, m[3] = {0.0, 0.0, 0.0};
@@ -372,4 +375,179 @@ int oracle_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ======================================================================================
+ * Synthetic von Karman inflow turbulence (paper App. F), evaluated by direct summation.
+ *
+ * Velocity of every equilibrium boundary cell at time step t:
+ *   cell set Gamma_VK: equilibrium cells on the west, east, south, north and top faces (never the
+ *   ground), each assigned to the first of those faces that contains it; optionally only cells
+ *   with U_b . n_f > 0 (n_f the inward normal).  A face whose characteristic speed U_c,f (|mean
+ *   U_b| or |mean U_b . n_f|) is <= 1e-7 is dropped.
+ *   u_ref = mean |U_b| and e_c = sum U_b / |sum U_b| over the kept cells ((1,0,0) if the sum is 0).
+ *   per face and mode m (m = 1..N_m): xi = (m - 1 + r)/N_m, k = exp(ln kmin + xi (ln kmax - ln kmin)),
+ *     kmin = 2 pi/(10 L), kmax = pi (kmin -> 0.1 kmax if kmin >= kmax); k_vec = k (sqrt(1-mu^2) cos th,
+ *     sqrt(1-mu^2) sin th, mu); W = k^4 / (1 + (k L)^2)^(17/6); A = sqrt(W) / sqrt(1/2 sum sqrt(W)^2);
+ *     A_a = g_a A; omega = u_ref k_vec . e_c
+ *   q_a(x, t) = sum_m A_a cos(k_vec . x + omega t + phi_a)   (x = integer cell indices)
+ *   sigma = I u_char (I > 0) or sigma0; u_char = |U_b| or |U_b . n_f|
+ *   temporal stride s: anchors t_a = floor(t/s) s; hold q(t_a) or interpolate linearly to t_a + s
+ *   U = U_b + sigma q
+ * Random inputs (readings: App. F states the distributions of r, mu, theta; phases uniform in
+ * [0, 2 pi)): rnd[f][m][6] = uniforms in [0,1) giving r, (mu+1)/2, theta/(2 pi), phi_x/(2 pi),
+ * phi_y/(2 pi), phi_z/(2 pi); f = face index 0..5 in the order x- x+ y- y+ z- z+ (z- unused).
+ * Output ueq (N x 3): the velocity of every equilibrium cell (U_b where no turbulence applies).
+ * ====================================================================================== */
+typedef struct {
+    int n_modes;
+    double L;           /* integral length scale (lattice units) */
+    double I;           /* turbulence intensity; <= 0 selects sigma0 */
+    double sigma0;
+    double gain[3];
+    int char_normal;    /* 1: characteristic speeds use the face-normal component */
+    int inflow_only;    /* 1: only cells with U_b . n_f > 0 */
+    int stride;         /* >= 1 */
+    int interpolate;    /* 1: linear between anchors, 0: hold */
+} oracle_stg_params;
+
+static const int stg_faces[5] = {0, 1, 2, 3, 5};   /* west, east, south, north, top */
+
+static void face_normal_in(int f, double n[3])
+{
+    n[0] = n[1] = n[2] = 0.0;
+    n[f / 2] = (f % 2 == 0) ? 1.0 : -1.0;
+}
+
+/* the STG face a cell belongs to (-1 if none) */
+static int stg_face_of(int x, int y, int z, int nx, int ny, int nz, const int face[6])
+{
+    const int p[3] = {x, y, z}, n[3] = {nx, ny, nz};
+    for (int k = 0; k < 5; ++k) {
+        const int f = stg_faces[k], a = f / 2;
+        if (face[f] != OR_INFLOW) continue;
+        if ((f % 2 == 0 && p[a] == 0) || (f % 2 == 1 && p[a] == n[a] - 1)) return f;
+    }
+    return -1;
+}
+
+static void stg_q(const double *tab, int nm, const double x[3], double t, double q[3])
+{
+    /* tab per mode: kx ky kz omega Ax Ay Az phix phiy phiz */
+    q[0] = q[1] = q[2] = 0.0;
+    for (int m = 0; m < nm; ++m) {
+        const double *T = tab + 10 * m;
+        const double base = T[0] * x[0] + T[1] * x[1] + T[2] * x[2] + T[3] * t;
+        for (int a = 0; a < 3; ++a) q[a] += T[4 + a] * cos(base + T[7 + a]);
+    }
+}
+
+int oracle_stg(const uint8_t *kind, int nx, int ny, int nz, const int face[6], const double *ub,
+               const oracle_stg_params *P, const double *rnd, long long t, double *ueq)
+{
+    const size_t N = (size_t)nx * ny * nz;
+    const int nm = P->n_modes;
+    if (nm < 1 || P->L <= 0.0 || P->stride < 1) return -1;
+    /* 1. cell sets, face means, global u_ref and e_c */
+    double sumU[6][3] = {{0}};
+    long long cnt[6] = {0};
+    for (size_t c = 0; c < N; ++c) {
+        if (kind[c] != OR_EQ) continue;
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((size_t)nx * ny));
+        const int f = stg_face_of(x, y, z, nx, ny, nz, face);
+        if (f < 0) continue;
+        double n[3];
+        face_normal_in(f, n);
+        const double *U = ub + 3 * z;
+        if (P->inflow_only && U[0] * n[0] + U[1] * n[1] + U[2] * n[2] <= 0.0) continue;
+        for (int a = 0; a < 3; ++a) sumU[f][a] += U[a];
+        cnt[f]++;
+    }
+    int keep[6] = {0};
+    for (int f = 0; f < 6; ++f) {
+        if (!cnt[f]) continue;
+        double mean[3], n[3];
+        face_normal_in(f, n);
+        for (int a = 0; a < 3; ++a) mean[a] = sumU[f][a] / cnt[f];
+        const double Uc = P->char_normal ? fabs(mean[0] * n[0] + mean[1] * n[1] + mean[2] * n[2])
+                                         : sqrt(mean[0] * mean[0] + mean[1] * mean[1] + mean[2] * mean[2]);
+        keep[f] = Uc > 1e-7;
+    }
+    double uref = 0.0, S[3] = {0.0, 0.0, 0.0};
+    long long ntot = 0;
+    for (size_t c = 0; c < N; ++c) {
+        if (kind[c] != OR_EQ) continue;
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((size_t)nx * ny));
+        const int f = stg_face_of(x, y, z, nx, ny, nz, face);
+        if (f < 0 || !keep[f]) continue;
+        double n[3];
+        face_normal_in(f, n);
+        const double *U = ub + 3 * z;
+        if (P->inflow_only && U[0] * n[0] + U[1] * n[1] + U[2] * n[2] <= 0.0) continue;
+        uref += sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+        for (int a = 0; a < 3; ++a) S[a] += U[a];
+        ntot++;
+    }
+    if (ntot) uref /= (double)ntot;
+    double ec[3] = {1.0, 0.0, 0.0};
+    const double Sn = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    if (Sn > 0.0) for (int a = 0; a < 3; ++a) ec[a] = S[a] / Sn;
+    /* 2. mode tables */
+    const double pi = 3.14159265358979323846;
+    double kmin = 2.0 * pi / (10.0 * P->L), kmax = pi;
+    if (kmin >= kmax) kmin = 0.1 * kmax;
+    double *tab = (double *)calloc((size_t)6 * nm * 10, sizeof(double));
+    if (!tab) return -2;
+    for (int f = 0; f < 6; ++f) {
+        if (!keep[f]) continue;
+        double *T = tab + (size_t)f * nm * 10;
+        double suma2 = 0.0;
+        for (int m = 0; m < nm; ++m) {
+            const double *R = rnd + ((size_t)f * nm + m) * 6;
+            const double xi = (m + R[0]) / nm;
+            const double k = exp(log(kmin) + xi * (log(kmax) - log(kmin)));
+            const double mu = 2.0 * R[1] - 1.0, th = 2.0 * pi * R[2];
+            const double s = sqrt(1.0 - mu * mu);
+            T[10 * m + 0] = k * s * cos(th);
+            T[10 * m + 1] = k * s * sin(th);
+            T[10 * m + 2] = k * mu;
+            T[10 * m + 3] = uref * (T[10 * m] * ec[0] + T[10 * m + 1] * ec[1] + T[10 * m + 2] * ec[2]);
+            const double W = pow(k, 4) / pow(1.0 + (k * P->L) * (k * P->L), 17.0 / 6.0);
+            T[10 * m + 4] = sqrt(W); /* raw amplitude, normalised below */
+            suma2 += W;
+            for (int a = 0; a < 3; ++a) T[10 * m + 7 + a] = 2.0 * pi * R[3 + a];
+        }
+        const double norm = sqrt(0.5 * suma2);
+        for (int m = 0; m < nm; ++m) {
+            const double A = T[10 * m + 4] / norm;
+            for (int a = 0; a < 3; ++a) T[10 * m + 4 + a] = P->gain[a] * A;
+        }
+    }
+    /* 3. boundary velocities */
+    const long long ta = (t / P->stride) * P->stride;
+    const double alpha = (double)(t - ta) / P->stride;
+    for (size_t c = 0; c < N; ++c) {
+        if (kind[c] != OR_EQ) { ueq[3 * c] = ueq[3 * c + 1] = ueq[3 * c + 2] = 0.0; continue; }
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((size_t)nx * ny));
+        const double *U = ub + 3 * z;
+        for (int a = 0; a < 3; ++a) ueq[3 * c + a] = U[a];
+        const int f = stg_face_of(x, y, z, nx, ny, nz, face);
+        if (f < 0 || !keep[f]) continue;
+        double n[3];
+        face_normal_in(f, n);
+        const double Un = U[0] * n[0] + U[1] * n[1] + U[2] * n[2];
+        if (P->inflow_only && Un <= 0.0) continue;
+        const double uchar = P->char_normal ? fabs(Un) : sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+        const double sigma = P->I > 0.0 ? P->I * uchar : P->sigma0;
+        const double X[3] = {(double)x, (double)y, (double)z};
+        double q[3], q2[3];
+        stg_q(tab + (size_t)f * nm * 10, nm, X, (double)ta, q);
+        if (P->interpolate && alpha > 0.0) {
+            stg_q(tab + (size_t)f * nm * 10, nm, X, (double)(ta + P->stride), q2);
+            for (int a = 0; a < 3; ++a) q[a] = (1.0 - alpha) * q[a] + alpha * q2[a];
+        }
+        for (int a = 0; a < 3; ++a) ueq[3 * c + a] = U[a] + sigma * q[a];
+    }
+    free(tab);
+    return 0;
 }

@@ -68,12 +68,14 @@ def lib() -> ctypes.CDLL:
         L.oracle_classify.restype = I
         L.oracle_expand_profile.argtypes = [P, I, I, D, P]
         L.oracle_expand_profile.restype = I
-        L.oracle_init.argtypes = [P, P, I, I, I, P, P, P, D]
+        L.oracle_init.argtypes = [P, P, I, I, I, P, P, P, D, P]
         L.oracle_init.restype = I
-        L.oracle_step.argtypes = [P, P, P, I, I, I, P, P, D, D, D, P, I, I, P, P, P]
+        L.oracle_step.argtypes = [P, P, P, I, I, I, P, P, D, D, D, P, I, I, P, P, P, P]
         L.oracle_step.restype = I
-        L.oracle_macros.argtypes = [P, P, I, I, I, P, D, P, P, P]
+        L.oracle_macros.argtypes = [P, P, I, I, I, P, D, P, P, P, P]
         L.oracle_macros.restype = I
+        L.oracle_stg.argtypes = [P, I, I, I, P, P, P, P, ctypes.c_longlong, P]
+        L.oracle_stg.restype = I
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = I
         _lib = L
@@ -138,22 +140,29 @@ def expand_profile(speed, nz: int, theta: float) -> np.ndarray:
     return ub
 
 
-def init(kind: np.ndarray, ub: np.ndarray, rho=None, u=None, rho_b: float = 1.0) -> np.ndarray:
+def _opt(a):
+    return None if a is None else np.ascontiguousarray(a, np.float64)
+
+
+def init(kind: np.ndarray, ub: np.ndarray, rho=None, u=None, rho_b: float = 1.0,
+         ueq=None) -> np.ndarray:
     nz, ny, nx = kind.shape
     F = np.zeros((19, nz, ny, nx), np.float64)
     rho = None if rho is None else np.ascontiguousarray(rho, np.float64)
     u = None if u is None else np.ascontiguousarray(u, np.float64)
     ub = np.ascontiguousarray(ub, np.float64)
+    ueq = _opt(ueq)
     lib().oracle_init(_p(F), _p(np.ascontiguousarray(kind, np.uint8)), nx, ny, nz,
-                      _p(rho), _p(u), _p(ub), float(rho_b))
+                      _p(rho), _p(u), _p(ub), float(rho_b), _p(ueq))
     return F
 
 
 def step(F: np.ndarray, kind: np.ndarray, faces, ub: np.ndarray, tau: float, C: float,
          force=None, rho_b: float = 1.0, z0: int = 0, z1: int | None = None,
-         out: np.ndarray | None = None, diag: bool = False, omega=None):
+         out: np.ndarray | None = None, diag: bool = False, omega=None, ueq=None):
     """One time step (pull form).  Returns F_next, or (F_next, Q, tau_eff) if ``diag``.
-    ``omega``: Coriolis rotation vector (lattice units), None = no Coriolis force."""
+    ``omega``: Coriolis rotation vector (lattice units), None = no Coriolis force.
+    ``ueq``: per-cell velocity (nz, ny, nx, 3) of the equilibrium cells, None = ``ub`` by height."""
     nz, ny, nx = kind.shape
     if out is None:
         out = np.zeros_like(F)
@@ -163,9 +172,11 @@ def step(F: np.ndarray, kind: np.ndarray, faces, ub: np.ndarray, tau: float, C: 
         q = np.zeros((nz, ny, nx), np.float64)
         te = np.zeros((nz, ny, nx), np.float64)
     om = None if omega is None else np.ascontiguousarray(omega, np.float64)
+    ue = _opt(ueq)
     lib().oracle_step(_p(F), _p(out), _p(kind), nx, ny, nz, _p(_faces(faces)),
                       _p(np.ascontiguousarray(ub, np.float64)), float(rho_b), float(tau), float(C),
-                      _p(fz), int(z0), int(nz if z1 is None else z1), _p(q), _p(te), _p(om))
+                      _p(fz), int(z0), int(nz if z1 is None else z1), _p(q), _p(te), _p(om),
+                      _p(ue))
     return (out, q, te) if diag else out
 
 
@@ -179,14 +190,53 @@ def run(F: np.ndarray, nsteps: int, *args, **kw) -> np.ndarray:
     return a
 
 
-def macros(F: np.ndarray, kind: np.ndarray, ub: np.ndarray, rho_b: float = 1.0, force=None):
+def macros(F: np.ndarray, kind: np.ndarray, ub: np.ndarray, rho_b: float = 1.0, force=None,
+           ueq=None):
     nz, ny, nx = kind.shape
     rho = np.zeros((nz, ny, nx), np.float64)
     u = np.zeros((nz, ny, nx, 3), np.float64)
     fz = None if force is None else np.ascontiguousarray(force, np.float64)
+    ue = _opt(ueq)
     lib().oracle_macros(_p(F), _p(kind), nx, ny, nz, _p(np.ascontiguousarray(ub, np.float64)),
-                        float(rho_b), _p(fz), _p(rho), _p(u))
+                        float(rho_b), _p(fz), _p(rho), _p(u), _p(ue))
     return rho, u
+
+
+class StgParams(ctypes.Structure):
+    """Parameters of the synthetic inflow turbulence (mirrors ``oracle_stg_params``)."""
+    _fields_ = [("n_modes", ctypes.c_int), ("L", ctypes.c_double), ("I", ctypes.c_double),
+                ("sigma0", ctypes.c_double), ("gain", ctypes.c_double * 3),
+                ("char_normal", ctypes.c_int), ("inflow_only", ctypes.c_int),
+                ("stride", ctypes.c_int), ("interpolate", ctypes.c_int)]
+
+
+def stg_params(n_modes=64, L=20.0, I=0.1, sigma0=0.0, gain=(1.0, 1.0, 1.0), char_normal=False,
+               inflow_only=False, stride=1, interpolate=True) -> StgParams:
+    p = StgParams()
+    p.n_modes, p.L, p.I, p.sigma0 = int(n_modes), float(L), float(I), float(sigma0)
+    for a in range(3):
+        p.gain[a] = float(gain[a])
+    p.char_normal, p.inflow_only = int(bool(char_normal)), int(bool(inflow_only))
+    p.stride, p.interpolate = int(stride), int(bool(interpolate))
+    return p
+
+
+def stg(kind: np.ndarray, faces, ub: np.ndarray, params: StgParams, rnd: np.ndarray,
+        t: int) -> np.ndarray:
+    """Velocity (nz, ny, nx, 3) of the equilibrium cells at step ``t`` with synthetic inflow
+    turbulence; ``rnd`` (6, n_modes, 6) uniforms in [0, 1) per face (x-, x+, y-, y+, z-, z+) and
+    mode: r, (mu + 1)/2, theta/2pi, phi_x/2pi, phi_y/2pi, phi_z/2pi.  Zero at non-EQ cells."""
+    nz, ny, nx = kind.shape
+    rnd = np.ascontiguousarray(rnd, np.float64)
+    if rnd.shape != (6, params.n_modes, 6):
+        raise ValueError("rnd must be (6, n_modes, 6)")
+    out = np.zeros((nz, ny, nx, 3), np.float64)
+    rc = lib().oracle_stg(_p(np.ascontiguousarray(kind, np.uint8)), nx, ny, nz,
+                          _p(_faces(faces)), _p(np.ascontiguousarray(ub, np.float64)),
+                          ctypes.addressof(params), _p(rnd), int(t), _p(out))
+    if rc != 0:
+        raise ValueError(f"oracle_stg failed ({rc})")
+    return out
 
 
 def num_threads() -> int:

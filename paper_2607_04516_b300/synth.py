@@ -224,3 +224,15 @@ def random_small_case(nx: int, ny: int, nz: int, faces, seed: int, solid_fractio
     speed = u_amp * (0.5 + 0.5 * rng.random(nz))
     return Case(f"rand{nx}x{ny}x{nz}", solid, tuple(faces), tau, cs, speed, theta, u0=u0,
                 rho0=rho0)
+
+
+def stg_uniforms(n_modes: int, seed: int, shared: bool = False) -> np.ndarray:
+    """Random draws of the synthetic inflow turbulence (App. F): (6, n_modes, 6) uniforms on [0, 1)
+    per face (x-, x+, y-, y+, z-, z+) and mode -- r_m, (mu_m + 1)/2, theta_m / 2pi and the three
+    phases / 2pi.  Each face gets its own stream seeded from (seed, face) unless ``shared``, in
+    which case every face gets the same realisation.  Only random numbers: no method arithmetic."""
+    out = np.empty((6, n_modes, 6), np.float64)
+    for f in range(6):
+        rng = np.random.default_rng([seed, 0 if shared else f + 1])
+        out[f] = rng.random((n_modes, 6))
+    return out
