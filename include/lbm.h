@@ -189,6 +189,69 @@ lbm_status lbm_diagnostics(lbm_domain *d, double *out);
  * rounding, not bit for bit. */
 lbm_status lbm_diagnostics_noalloc(lbm_domain *d, double *out);
 
+/* ---------------------------------------------------------------------------------------------
+ * Synthetic von Karman inflow turbulence (App. F).
+ *
+ * Once configured, every lbm_step first sets the velocity of the equilibrium cells of the inflow
+ * faces x-, x+, y-, y+ and z+ (never the ground) to
+ *     U_i(t) = U_b,i + sigma_i q^(f)(x_i, t),   q_a = sum_m A_m,a cos(k_m . x_i + omega_m t + phi_m,a)
+ * for the step t about to be taken (t = lbm_steps_done), one extra kernel per step; that step's
+ * equilibrium cells then hold f^eq(rho_b, U_i(t)).  x_i are the integer cell indices.  Each cell
+ * belongs to the first inflow face holding it in the order x-, x+, y-, y+, z+.  Per face f:
+ * cells = its equilibrium cells, restricted to U_b . n_f > 0 (n_f inward) if inflow_only; the face
+ * is dropped (its cells keep U_b) when it has none or U_c,f = |mean U_b| (|mean U_b . n_f| with
+ * char_normal) is <= 1e-7.  Over the kept cells: u_ref = mean |U_b|, e_c = sum U_b / |sum U_b|
+ * ((1,0,0) if the sum is 0), omega_m = u_ref k_m . e_c.  Wavenumbers k_m = exp(ln k_min + xi_m
+ * (ln k_max - ln k_min)), xi_m = (m - 1 + r_m)/N_m, k_min = 2 pi/(10 L), k_max = pi (k_min -> 0.1
+ * k_max if k_min >= k_max); directions (sqrt(1-mu^2) cos theta, sqrt(1-mu^2) sin theta, mu); von
+ * Karman weights W = k^4 / (1 + (k L)^2)^(17/6), A_m = sqrt(W_m) / sqrt(1/2 sum W), A_m,a = g_a A_m;
+ * sigma_i = I u_char (I > 0; u_char = |U_b,i| or |U_b,i . n_f|) else sigma0.  With a stride s the
+ * field is evaluated at anchors t_a = floor(t/s) s and held, or interpolated linearly to t_a + s.
+ * The step's velocity readouts (lbm_macroscopic, lbm_sample_columns, lbm_diagnostics) report U_i of
+ * the last step taken; right after lbm_init_fields (which uses U_b) they report U_b.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct {
+    int n_modes;        /* N_m, 1 .. 1024 (same for every face) */
+    float length;       /* integral length scale L, lattice units, > 0 */
+    float intensity;    /* I > 0: sigma_i = I u_char; I <= 0: sigma_i = sigma0 */
+    float sigma0;       /* constant fluctuation level (lattice velocity), >= 0 */
+    float gain[3];      /* component gains g_x, g_y, g_z */
+    int char_normal;    /* 0: U_c,f and u_char from |U_b|; 1: from the face-normal component */
+    int inflow_only;    /* 1: only cells with U_b . n_f > 0 are turbulent */
+    int stride;         /* temporal stride s >= 1 */
+    int interpolate;    /* 1: interpolate between anchors, 0: hold the anchor's field */
+} lbm_stg_params;
+
+/* Defaults: 64 modes, L = 20, I = 0.1, sigma0 = 0, gains 1, |U_b| speeds, every cell, stride 1,
+ * interpolation on.  LBM_EINVAL if p is NULL. */
+lbm_status lbm_stg_params_default(lbm_stg_params *p);
+
+/* Device bytes lbm_stg_configure needs for n_modes modes on this domain's inflow faces (tables
+ * and per-face velocity planes); 0 if d is NULL, n_modes is out of range or the domain has no
+ * inflow face among x-, x+, y-, y+, z+. */
+size_t lbm_stg_workspace_bytes(const lbm_domain *d, int n_modes);
+
+/* Switch the synthetic inflow on (or reconfigure it) for later steps.
+ *   p          parameters (host), checked: LBM_EINVAL with a message when out of range
+ *   uniforms   HOST double[6][n_modes][6], values in [0, 1): for face f (x-, x+, y-, y+, z-, z+;
+ *              the z- entries are unused) and mode m: r_m, (mu_m + 1)/2, theta_m / 2 pi, and
+ *              phi_m,x, phi_m,y, phi_m,z / 2 pi.  The paper draws them from a base seed mixed
+ *              with the face id; here the caller draws them (the same numbers on every face give
+ *              one shared realisation).  Copied during the call.
+ *   workspace  DEVICE memory, 256-byte aligned, ws_bytes >= lbm_stg_workspace_bytes; owned by
+ *              the caller, used until lbm_stg_disable / lbm_destroy or the next configure
+ * The tables depend on the inflow profile: lbm_set_inflow_profile rebuilds them.  Builds the
+ * tables on the host (O(N_m x face cells)) and uploads them on the domain's stream. */
+lbm_status lbm_stg_configure(lbm_domain *d, const lbm_stg_params *p, const double *uniforms,
+                             void *workspace, size_t ws_bytes);
+
+/* Switch the synthetic inflow off: the equilibrium cells take U_b again from the next step on. */
+lbm_status lbm_stg_disable(lbm_domain *d);
+
+/* The configuration's global convection quantities: u_ref, e_c[3] (HOST) and a bit mask of the
+ * turbulent faces (bit k = face k).  Any output may be NULL.  LBM_EINVAL when not configured. */
+lbm_status lbm_stg_reference(const lbm_domain *d, double *u_ref, double *e_c, int *faces);
+
 /* Message of the last failed call on this domain ("" if none).  Never NULL. */
 const char *lbm_last_error(const lbm_domain *d);
 

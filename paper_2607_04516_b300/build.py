@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liblbm.so")
 SOURCES = [os.path.join(CSRC, "lbm_kernels.cu"), os.path.join(CSRC, "lbm_capi.cu"),
-           os.path.join(CSRC, "lbm_noalloc.cu")]
+           os.path.join(CSRC, "lbm_noalloc.cu"), os.path.join(CSRC, "lbm_stg.cu")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

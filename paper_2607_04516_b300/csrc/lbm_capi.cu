@@ -12,6 +12,7 @@
 
 #include "lbm.h"
 #include "lbm_internal.h"
+#include "lbm_stg.h"
 
 using namespace lbm;
 
@@ -97,6 +98,8 @@ struct lbm_domain {
     Layout L;
     long long t;                 // steps since init
     std::vector<float> ub_host;  // expanded profile staging
+    std::vector<uint8_t> face_solid[6];   // solid mask on each face plane (n1 fastest)
+    StgState stg;                // synthetic inflow turbulence (App. F)
     char err[512];
 };
 
@@ -146,7 +149,20 @@ StepArgs args_of(const lbm_domain *d) {
     a.zface_begin = xs * d->ny * d->nz + ys * ix * d->nz;
     a.zfast = zfast_mask(a.g);
     a.pack16 = (d->p.store != LBM_F32 && d->N % 2 == 0 && d->nx % 2 == 0) ? 1 : 0;
+    if (d->stg.on && d->stg.valid)
+        for (int k = 0; k < d->stg.L.nfaces; ++k) a.ueq[d->stg.L.f[k].face] = d->stg.L.f[k].ueq;
     return a;
+}
+
+// Rebuild the synthetic-inflow tables for the current profile and upload them.
+lbm_status stg_rebuild(lbm_domain *d) {
+    const StepArgs a = args_of(d);
+    const char *msg = stg_build(d->stg, a.g, d->ub_host.data(), d->face_solid, a.ub, a.flags);
+    if (msg) return fail(d, LBM_EINVAL, "%s", msg);
+    d->stg.valid = false;
+    if (d->stg.table_bytes == 0) return LBM_OK;
+    return cuda_check(d, cudaMemcpyAsync(d->stg.ws, d->stg.image.data(), d->stg.table_bytes,
+                                         cudaMemcpyHostToDevice, d->stream), "stg table upload");
 }
 
 bool has_force(const lbm_domain *d) {
@@ -234,6 +250,20 @@ lbm_status lbm_create_domain(const uint8_t *solid, int nx, int ny, int nz, const
     d->t = 0;
     d->err[0] = 0;
     d->ub_host.assign((size_t)nz * 3, 0.0f);
+    for (int k = 0; k < 6; ++k) {
+        // face plane k: (y, z), (x, z) or (x, y), first index fastest
+        const int a = k / 2, hi = k & 1;
+        const int n1 = a == 0 ? ny : nx, n2 = a == 2 ? ny : nz;
+        d->face_solid[k].assign((size_t)n1 * n2, 0);
+        for (int j = 0; j < n2; ++j)
+            for (int i = 0; i < n1; ++i) {
+                const int x = a == 0 ? (hi ? nx - 1 : 0) : i;
+                const int y = a == 1 ? (hi ? ny - 1 : 0) : (a == 0 ? i : j);
+                const int z = a == 2 ? (hi ? nz - 1 : 0) : j;
+                d->face_solid[k][(size_t)i + (size_t)n1 * j] =
+                    solid[(size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z)] ? 1 : 0;
+            }
+    }
 
     StepArgs a = args_of(d);
     // the population region doubles as staging for the mask (it is initialised right after)
@@ -286,12 +316,15 @@ lbm_status lbm_set_inflow_profile(lbm_domain *d, const float *speed, int L, floa
         d->ub_host[3 * k + 1] = (float)(v * s);
         d->ub_host[3 * k + 2] = 0.0f;
     }
-    return cuda_check(d, cudaMemcpyAsync(d->ws + d->L.ub, d->ub_host.data(), (size_t)nz * 3 * sizeof(float),
-                                         cudaMemcpyHostToDevice, d->stream), "profile upload");
+    lbm_status st = cuda_check(d, cudaMemcpyAsync(d->ws + d->L.ub, d->ub_host.data(), (size_t)nz * 3 * sizeof(float),
+                                                  cudaMemcpyHostToDevice, d->stream), "profile upload");
+    if (st == LBM_OK && d->stg.on) st = stg_rebuild(d);
+    return st;
 }
 
 lbm_status lbm_init_fields(lbm_domain *d, const float *rho, const float *u) {
     if (!d) return LBM_EINVAL;
+    d->stg.valid = false;   // equilibrium cells start from u_b
     const StepArgs a = args_of(d);
     lbm_status st = cuda_check(d, launch_init(d->p.store, a, rho, u, d->stream), "init kernel");
     if (st == LBM_OK) d->t = 0;
@@ -313,9 +346,18 @@ lbm_status lbm_diagnostics(lbm_domain *d, double *out) {
 lbm_status lbm_step(lbm_domain *d, int n) {
     if (!d) return LBM_EINVAL;
     if (n < 0) return fail(d, LBM_EINVAL, "step: n must be >= 0");
-    const StepArgs a = args_of(d);
     const bool force = has_force(d);
     for (int k = 0; k < n; ++k) {
+        if (d->stg.on) {
+            // U(t) of the inflow faces; with a held stride only at anchors
+            const StgState &s = d->stg;
+            if (!s.valid || s.p.interpolate || d->t % s.p.stride == 0) {
+                lbm_status st = cuda_check(d, launch_stg(s, d->t, d->stream), "stg kernel launch");
+                if (st != LBM_OK) return st;
+            }
+            d->stg.valid = true;
+        }
+        const StepArgs a = args_of(d);
         launch_step(d->p.store, (d->t & 1) == 0, force, a, d->stream);
         d->t += 1;
         if (d->p.watchdog_every > 0 && d->t % d->p.watchdog_every == 0) {
@@ -353,6 +395,64 @@ lbm_status lbm_export_populations(lbm_domain *d, float *g) {
     if (!g) return fail(d, LBM_EINVAL, "export: NULL pointer");
     const StepArgs a = args_of(d);
     return cuda_check(d, launch_export(d->p.store, a, (d->t & 1) != 0, g, d->stream), "export kernel");
+}
+
+lbm_status lbm_stg_params_default(lbm_stg_params *p) {
+    if (!p) return LBM_EINVAL;
+    std::memset(p, 0, sizeof(*p));
+    p->n_modes = 64;
+    p->length = 20.0f;
+    p->intensity = 0.1f;
+    p->sigma0 = 0.0f;
+    p->gain[0] = p->gain[1] = p->gain[2] = 1.0f;
+    p->stride = 1;
+    p->interpolate = 1;
+    return LBM_OK;
+}
+
+size_t lbm_stg_workspace_bytes(const lbm_domain *d, int n_modes) {
+    if (!d) return 0;
+    return stg_workspace_bytes(args_of(d).g, n_modes);
+}
+
+lbm_status lbm_stg_configure(lbm_domain *d, const lbm_stg_params *p, const double *uniforms,
+                             void *workspace, size_t ws_bytes) {
+    if (!d) return LBM_EINVAL;
+    if (const char *msg = stg_check(p)) return fail(d, LBM_EINVAL, "%s", msg);
+    if (!uniforms || !workspace) return fail(d, LBM_EINVAL, "stg: NULL uniforms or workspace");
+    if ((uintptr_t)workspace % kAlign) return fail(d, LBM_EINVAL, "stg: workspace not 256-byte aligned");
+    const size_t need = stg_workspace_bytes(args_of(d).g, p->n_modes);
+    if (need == 0) return fail(d, LBM_EINVAL, "stg: the domain has no inflow face among x-, x+, y-, y+, z+");
+    if (ws_bytes < need) return fail(d, LBM_ENOMEM, "stg: workspace has %zu bytes, needs %zu", ws_bytes, need);
+    const size_t nr = (size_t)6 * p->n_modes * 6;
+    for (size_t i = 0; i < nr; ++i)
+        if (!(uniforms[i] >= 0.0 && uniforms[i] < 1.0)) return fail(d, LBM_EINVAL, "stg: uniforms[%zu] outside [0, 1)", i);
+    StgState &s = d->stg;
+    s.on = false;
+    s.p = *p;
+    s.rnd.assign(uniforms, uniforms + nr);
+    s.ws = (char *)workspace;
+    s.ws_bytes = ws_bytes;
+    lbm_status st = stg_rebuild(d);
+    if (st != LBM_OK) return st;
+    s.on = true;
+    s.valid = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_stg_disable(lbm_domain *d) {
+    if (!d) return LBM_EINVAL;
+    d->stg.on = false;
+    d->stg.valid = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_stg_reference(const lbm_domain *d, double *u_ref, double *e_c, int *faces) {
+    if (!d || !d->stg.on) return LBM_EINVAL;
+    if (u_ref) *u_ref = d->stg.u_ref;
+    if (e_c) for (int c = 0; c < 3; ++c) e_c[c] = d->stg.e_c[c];
+    if (faces) *faces = d->stg.kept;
+    return LBM_OK;
 }
 
 const char *lbm_last_error(const lbm_domain *d) { return d ? d->err : "no domain"; }

@@ -75,7 +75,7 @@ LBM_HD void cell_init(const StepArgs &a, long long n, const float *__restrict__ 
     float drho, ux, uy, uz;
     if (fl & F_EQ) {
         drho = a.rho_b - 1.0f;
-        ux = a.ub[3 * z]; uy = a.ub[3 * z + 1]; uz = a.ub[3 * z + 2];
+        eq_velocity(a, n, ux, uy, uz);
     } else {
         drho = rho ? rho[n] - 1.0f : 0.0f;
         if (u) { ux = u[3 * n]; uy = u[3 * n + 1]; uz = u[3 * n + 2]; }
@@ -108,8 +108,7 @@ LBM_HD void cell_local(const StepArgs &a, int n) {
     const uint8_t fl = a.flags[n];
     if (fl & F_SOLID) return;
     if (fl & F_EQ) {
-        const int z = (int)(n / a.g.sz);
-        equilibrium_shifted(a.rho_b - 1.0f, a.ub[3 * z], a.ub[3 * z + 1], a.ub[3 * z + 2], g);
+        eq_cell_g(a, n, g);
     } else {
         collide<FORCE>(g, a);
     }
@@ -229,7 +228,9 @@ LBM_HD void cell_neighbor_face(const StepArgs &a, uint8_t fl, int x, int y, int 
     float g[Q];
     const bool fluid = !(fl & F_EQ);
     if (!fluid) {
-        equilibrium_shifted(a.rho_b - 1.0f, a.ub[3 * z], a.ub[3 * z + 1], a.ub[3 * z + 2], g);
+        float ux, uy, uz;
+        eq_velocity(a, x, y, z, ux, uy, uz);
+        equilibrium_shifted(a.rho_b - 1.0f, ux, uy, uz, g);
     } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -293,8 +294,7 @@ LBM_HD void cell2_local(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
         const int n = c ? n1 : n0;
         float g[Q];
         if (fl & F_EQ) {
-            const int z = (int)(n / a.g.sz);
-            equilibrium_shifted(a.rho_b - 1.0f, a.ub[3 * z], a.ub[3 * z + 1], a.ub[3 * z + 2], g);
+            eq_cell_g(a, n, g);
         } else {
 #pragma unroll
             for (int i = 0; i < Q; ++i) g[i] = Cd::dec_bits(c ? pk[i] >> 16 : pk[i] & 0xffffu);
@@ -362,8 +362,7 @@ LBM_HD void cellp_local(const StepArgs &a, int n0) {
         if (fl & F_SOLID) continue;
         float g[Q];
         if (fl & F_EQ) {
-            const int z = (int)((n0 + c) / a.g.sz);
-            equilibrium_shifted(a.rho_b - 1.0f, a.ub[3 * z], a.ub[3 * z + 1], a.ub[3 * z + 2], g);
+            eq_cell_g(a, n0 + c, g);
         } else {
 #pragma unroll
             for (int i = 0; i < Q; ++i) g[i] = Cd::dec_bits(c ? pk[i] >> 16 : pk[i] & 0xffffu);
@@ -462,7 +461,9 @@ LBM_HD void read_post(const StepArgs &a, long long n, uint8_t fl, bool layoutA, 
     cell_coords(a.g, n, x, y, z);
     if (fl & F_EQ) {
         // the equilibrium populations as stored (and as consumed by the neighbours)
-        equilibrium_shifted(a.rho_b - 1.0f, a.ub[3 * z], a.ub[3 * z + 1], a.ub[3 * z + 2], g);
+        float ux, uy, uz;
+        eq_velocity(a, x, y, z, ux, uy, uz);
+        equilibrium_shifted(a.rho_b - 1.0f, ux, uy, uz, g);
 #pragma unroll
         for (int j = 0; j < Q; ++j) g[j] = Cd::dec(Cd::enc(g[j]));
         return;
@@ -512,8 +513,8 @@ LBM_HD void cell_macros(const StepArgs &a, long long n, bool layoutA, float &r, 
     const uint8_t fl = a.flags[n];
     r = 0.0f; ux = 0.0f; uy = 0.0f; uz = 0.0f;
     if (fl & F_EQ) {
-        const int z = (int)(n / a.g.sz);
-        r = a.rho_b; ux = a.ub[3 * z]; uy = a.ub[3 * z + 1]; uz = a.ub[3 * z + 2];
+        r = a.rho_b;
+        eq_velocity(a, n, ux, uy, uz);
     } else if (!(fl & F_SOLID)) {
         float g[Q];
         read_post<S>(a, n, fl, layoutA, g);

@@ -181,6 +181,10 @@ struct StepArgs {
     int zfast;                  // bit 0 / bit 1: the z- / z+ face cells take the layer path
     int pack16;                 // 16-bit storage with N and nx even: lattice blocks update pairs of
                                 // adjacent cells with 4-byte accesses
+    const float4 *ueq[6];       // synthetic inflow turbulence (App. F): per inflow face x-, x+, y-,
+                                // y+, z+ the velocity of its equilibrium cells, [n2][n1] in the
+                                // face's plane (x+- : y + ny z; y+- : x + nx z; z+ : x + nx y);
+                                // all null = the equilibrium cells take u_b(z)
 };
 
 // The z face layers whose cells (with interior x and y) take the layer path: no-slip or free-slip
@@ -547,6 +551,39 @@ LBM_HD void cell_coords(const Geo &G, long long n, int &x, int &y, int &z) {
     const long long r = n - (long long)z * G.sz;
     y = (int)(r / G.sy);
     x = (int)(r - (long long)y * G.sy);
+}
+
+// Velocity of the equilibrium cell (x, y, z).  With synthetic inflow turbulence on, a cell on an
+// inflow face takes the value in the plane of the first inflow face holding it, in the order
+// x-, x+, y-, y+, z+ (each boundary cell belongs to one face, App. F); a cell on none of them (an
+// inflow ground) and every cell without turbulence take the profile u_b(z).
+LBM_HD void eq_velocity(const StepArgs &a, int x, int y, int z, float &ux, float &uy, float &uz) {
+    const Geo &G = a.g;
+    const float4 *p = nullptr;
+    if (a.ueq[0] && x == 0) p = a.ueq[0] + y + (long long)G.ny * z;
+    else if (a.ueq[1] && x == G.nx - 1) p = a.ueq[1] + y + (long long)G.ny * z;
+    else if (a.ueq[2] && y == 0) p = a.ueq[2] + x + (long long)G.nx * z;
+    else if (a.ueq[3] && y == G.ny - 1) p = a.ueq[3] + x + (long long)G.nx * z;
+    else if (a.ueq[5] && z == G.nz - 1) p = a.ueq[5] + x + (long long)G.nx * y;
+    if (p) {
+        const float4 v = *p;
+        ux = v.x; uy = v.y; uz = v.z;
+    } else {
+        ux = a.ub[3 * z]; uy = a.ub[3 * z + 1]; uz = a.ub[3 * z + 2];
+    }
+}
+
+LBM_HD void eq_velocity(const StepArgs &a, long long n, float &ux, float &uy, float &uz) {
+    int x, y, z;
+    cell_coords(a.g, n, x, y, z);
+    eq_velocity(a, x, y, z, ux, uy, uz);
+}
+
+// Shifted equilibrium of an equilibrium cell.
+LBM_HD void eq_cell_g(const StepArgs &a, long long n, float (&g)[Q]) {
+    float ux, uy, uz;
+    eq_velocity(a, n, ux, uy, uz);
+    equilibrium_shifted(a.rho_b - 1.0f, ux, uy, uz, g);
 }
 
 }  // namespace lbm

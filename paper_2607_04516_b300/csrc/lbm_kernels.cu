@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(kBlock) k_reduce_partial(StepArgs a, bool layo
         int x, y, z;
         cell_coords(a.g, n, x, y, z);
         if (fl & F_EQ) {
-            r = a.rho_b; ux = a.ub[3 * z]; uy = a.ub[3 * z + 1]; uz = a.ub[3 * z + 2];
+            r = a.rho_b;
+            eq_velocity(a, x, y, z, ux, uy, uz);
         } else {
             float g[Q];
             read_post<S>(a, n, fl, layoutA, g);

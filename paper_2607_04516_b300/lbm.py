@@ -35,6 +35,12 @@ class lbm_params(ctypes.Structure):
                 ("watchdog_every", ctypes.c_int), ("coriolis", ctypes.c_float * 3)]
 
 
+class lbm_stg_params(ctypes.Structure):
+    _fields_ = [("n_modes", ctypes.c_int), ("length", ctypes.c_float), ("intensity", ctypes.c_float),
+                ("sigma0", ctypes.c_float), ("gain", ctypes.c_float * 3), ("char_normal", ctypes.c_int),
+                ("inflow_only", ctypes.c_int), ("stride", ctypes.c_int), ("interpolate", ctypes.c_int)]
+
+
 # exported symbols and their ctypes signatures (the header is the authority)
 _P, _I, _F, _LL, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_longlong, ctypes.c_size_t
 _PP = ctypes.POINTER(lbm_params)
@@ -55,6 +61,11 @@ SIGNATURES = {
     "lbm_direction_table": (_I, [_P, _P]),
     "lbm_diagnostics": (_I, [_P, _P]),
     "lbm_diagnostics_noalloc": (_I, [_P, _P]),
+    "lbm_stg_params_default": (_I, [ctypes.POINTER(lbm_stg_params)]),
+    "lbm_stg_workspace_bytes": (_SZ, [_P, _I]),
+    "lbm_stg_configure": (_I, [_P, ctypes.POINTER(lbm_stg_params), _P, _P, _SZ]),
+    "lbm_stg_disable": (_I, [_P]),
+    "lbm_stg_reference": (_I, [_P, _P, _P, _P]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
     "lbm_destroy": (None, [_P]),
 }
@@ -193,6 +204,44 @@ def lbm_diagnostics_noalloc(dom, out):
     _check(load().lbm_diagnostics_noalloc(dom, _ptr(out)), dom)
 
 
+def make_stg_params(n_modes=64, length=20.0, intensity=0.1, sigma0=0.0, gain=(1.0, 1.0, 1.0),
+                    char_normal=False, inflow_only=False, stride=1, interpolate=True) -> lbm_stg_params:
+    p = lbm_stg_params()
+    load(False).lbm_stg_params_default(ctypes.byref(p))
+    p.n_modes, p.length, p.intensity, p.sigma0 = int(n_modes), float(length), float(intensity), float(sigma0)
+    for a in range(3):
+        p.gain[a] = float(gain[a])
+    p.char_normal, p.inflow_only = int(bool(char_normal)), int(bool(inflow_only))
+    p.stride, p.interpolate = int(stride), int(bool(interpolate))
+    return p
+
+
+def lbm_stg_workspace_bytes(dom, n_modes: int) -> int:
+    return load(False).lbm_stg_workspace_bytes(dom, int(n_modes))
+
+
+def lbm_stg_configure(dom, params: lbm_stg_params, uniforms: np.ndarray, workspace):
+    """``uniforms``: float64 (6, n_modes, 6) host array; ``workspace``: CUDA uint8 tensor."""
+    u = np.ascontiguousarray(uniforms, np.float64)
+    if u.shape != (6, params.n_modes, 6):
+        raise ValueError("uniforms must be (6, n_modes, 6)")
+    _check(load().lbm_stg_configure(dom, ctypes.byref(params), u.ctypes.data, _ptr(workspace),
+                                    workspace.numel() * workspace.element_size()), dom)
+
+
+def lbm_stg_disable(dom):
+    _check(load(False).lbm_stg_disable(dom), dom)
+
+
+def lbm_stg_reference(dom):
+    """(u_ref, e_c (3,), bit mask of turbulent faces)."""
+    u = ctypes.c_double()
+    e = np.zeros(3, np.float64)
+    f = ctypes.c_int()
+    _check(load(False).lbm_stg_reference(dom, ctypes.byref(u), e.ctypes.data, ctypes.byref(f)), dom)
+    return u.value, e, f.value
+
+
 def lbm_destroy(dom):
     load(False).lbm_destroy(dom)
 
@@ -272,6 +321,24 @@ class Domain:
 
     def diagnostics(self) -> dict:
         return lbm_diagnostics(self.dom)
+
+    def configure_stg(self, uniforms, **kw):
+        """Synthetic inflow turbulence (App. F) from the next step on; ``kw`` as make_stg_params,
+        ``uniforms`` (6, n_modes, 6) random draws (e.g. ``synth.stg_uniforms``)."""
+        import torch
+        p = make_stg_params(**kw)
+        nbytes = lbm_stg_workspace_bytes(self.dom, p.n_modes)
+        if nbytes == 0:
+            raise LbmError(-1, "no inflow face for synthetic turbulence, or n_modes out of range")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        lbm_stg_configure(self.dom, p, uniforms, ws)
+        self.stg_workspace = ws   # used by every later step; freed with the domain
+
+    def disable_stg(self):
+        lbm_stg_disable(self.dom)
+
+    def stg_reference(self):
+        return lbm_stg_reference(self.dom)
 
 
 def glups(cells: int, steps: int, seconds: float) -> float:

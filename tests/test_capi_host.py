@@ -150,3 +150,39 @@ def test_params_default_has_no_rotation(lib):
     assert tuple(p.coriolis) == (0.0, 0.0, 0.0)
     assert lbm.lbm_workspace_bytes(8, 8, 8, lbm.make_params(("periodic",) * 6,
                                                             coriolis=(0, 0, float("nan")))) == 0
+
+
+def test_stg_params_default_and_null_handles(lib):
+    p = lbm.make_stg_params()
+    assert (p.n_modes, p.length, p.intensity, p.sigma0) == (64, 20.0, pytest.approx(0.1), 0.0)
+    assert tuple(p.gain) == (1.0, 1.0, 1.0)
+    assert (p.char_normal, p.inflow_only, p.stride, p.interpolate) == (0, 0, 1, 1)
+    assert lib.lbm_stg_params_default(None) == -1
+    assert lib.lbm_stg_workspace_bytes(None, 8) == 0
+    assert lib.lbm_stg_configure(None, ctypes.byref(p), None, None, 0) == -1
+    assert lib.lbm_stg_disable(None) == -1
+    assert lib.lbm_stg_reference(None, None, None, None) == -1
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    """sizeof and every field offset of the parameter structs, as gcc lays them out from the
+    header, equal the binding's ctypes mirrors."""
+    structs = {"lbm_params": lbm.lbm_params, "lbm_stg_params": lbm.lbm_stg_params}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
