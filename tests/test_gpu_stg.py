@@ -110,7 +110,8 @@ def test_reference_speed_and_direction_are_the_brute_force_means():
     mask[:, :, 0] = True                                              # x- face
     mask[:, 0, :] = True                                              # y- face
     mask &= kind == orc.EQ
-    U = np.broadcast_to(ub[:, None, None, :], kind.shape + (3,))[mask]
+    ub32 = ub.astype(np.float32).astype(np.float64)                   # the library holds FP32 u_b
+    U = np.broadcast_to(ub32[:, None, None, :], kind.shape + (3,))[mask]
     assert u_ref == pytest.approx(np.linalg.norm(U, axis=1).mean(), rel=1e-12)
     s = U.sum(0)
     np.testing.assert_allclose(e_c, s / np.linalg.norm(s), rtol=0, atol=1e-14)
@@ -172,7 +173,8 @@ def test_disable_and_profile_change():
     mask[:, :, 0] = True
     mask[:, 0, :] = True
     mask &= eq
-    U = np.broadcast_to(ub2[:, None, None, :], kind.shape + (3,))[mask]
+    ub32 = ub2.astype(np.float32).astype(np.float64)
+    U = np.broadcast_to(ub32[:, None, None, :], kind.shape + (3,))[mask]
     assert u_ref == pytest.approx(np.linalg.norm(U, axis=1).mean(), rel=1e-12)
     # switched off: the equilibrium cells take u_b again from the next step on
     dom.disable_stg()
