@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--store", default="f32", choices=list(STORE_BYTES))
     ap.add_argument("--workload", default="city400", choices=list(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variants", default="f16s,bf16s,stg",
+    ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10",
                     help="extra storage kinds timed after the main measurement ('' = none)")
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -319,18 +319,21 @@ def run_ours(args, rank, world):
 
     variants = {}
     for st in [v for v in args.variants.split(",") if v and v != args.store]:
-        if st == "stg":
-            # FP32 with the synthetic von Karman inflow (App. F) on the inflow faces: 64 modes
+        if st in ("stg", "stg_s10"):
+            # FP32 with the synthetic von Karman inflow (App. F) on the inflow faces: 64 modes,
+            # evaluated every step, or every 10 steps with linear interpolation in between
             from paper_2607_04516_b300 import synth
+            stride = 10 if st == "stg_s10" else 1
             d2 = build_domain("f32")
-            d2.configure_stg(synth.stg_uniforms(64, seed=11), n_modes=64, length=20.0, intensity=0.1)
+            d2.configure_stg(synth.stg_uniforms(64, seed=11), n_modes=64, length=20.0, intensity=0.1,
+                             stride=stride, interpolate=True)
             K2 = max(200, args.steps // 4)
             t_ms, _, _, _, _ = time_steps(d2, K2, min(args.warmup, 200), world, None)
             t_ms = max_over_ranks(t_ms, world)
             g2 = weak_scaling_glups(N, K2, world, t_ms)
             variants[st] = {"glups": g2, "vs_f32": g2 / value if args.store == "f32" else None,
-                            "ms_per_step": t_ms / K2, "modes": 64,
-                            "launches_per_step": 2}
+                            "ms_per_step": t_ms / K2, "modes": 64, "stride": stride,
+                            "launches_per_step": 1 + 1 / stride}
             del d2
             torch.cuda.empty_cache()
             continue

@@ -192,11 +192,14 @@ lbm_status lbm_diagnostics_noalloc(lbm_domain *d, double *out);
 /* ---------------------------------------------------------------------------------------------
  * Synthetic von Karman inflow turbulence (App. F).
  *
- * Once configured, every lbm_step first sets the velocity of the equilibrium cells of the inflow
- * faces x-, x+, y-, y+ and z+ (never the ground) to
+ * Once configured, every lbm_step sets the velocity of the equilibrium cells of the inflow faces
+ * x-, x+, y-, y+ and z+ (never the ground) to
  *     U_i(t) = U_b,i + sigma_i q^(f)(x_i, t),   q_a = sum_m A_m,a cos(k_m . x_i + omega_m t + phi_m,a)
- * for the step t about to be taken (t = lbm_steps_done), one extra kernel per step; that step's
- * equilibrium cells then hold f^eq(rho_b, U_i(t)).  x_i are the integer cell indices.  Each cell
+ * for the step t about to be taken (t = lbm_steps_done); that step's equilibrium cells then hold
+ * f^eq(rho_b, U_i(t)).  One extra kernel evaluates the sum at each anchor t_a (every step with
+ * stride 1, every s steps otherwise); between anchors the step kernel itself blends the two
+ * anchor fields (interpolation) or keeps the last one (hold).  x_i are the integer cell indices.
+ * Each cell
  * belongs to the first inflow face holding it in the order x-, x+, y-, y+, z+.  Per face f:
  * cells = its equilibrium cells, restricted to U_b . n_f > 0 (n_f inward) if inflow_only; the face
  * is dropped (its cells keep U_b) when it has none or U_c,f = |mean U_b| (|mean U_b . n_f| with

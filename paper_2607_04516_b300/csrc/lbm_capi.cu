@@ -149,8 +149,14 @@ StepArgs args_of(const lbm_domain *d) {
     a.zface_begin = xs * d->ny * d->nz + ys * ix * d->nz;
     a.zfast = zfast_mask(a.g);
     a.pack16 = (d->p.store != LBM_F32 && d->N % 2 == 0 && d->nx % 2 == 0) ? 1 : 0;
-    if (d->stg.on && d->stg.valid)
-        for (int k = 0; k < d->stg.L.nfaces; ++k) a.ueq[d->stg.L.f[k].face] = d->stg.L.f[k].ueq;
+    if (d->stg.on && d->stg.valid) {
+        const StgState &s = d->stg;
+        for (int k = 0; k < s.L.nfaces; ++k) {
+            a.ueq[s.L.f[k].face] = s.plane[s.cur][k];
+            a.ueq_next[s.L.f[k].face] = s.plane[1 - s.cur][k];
+        }
+        a.ueq_alpha = s.alpha;
+    }
     return a;
 }
 
@@ -349,13 +355,26 @@ lbm_status lbm_step(lbm_domain *d, int n) {
     const bool force = has_force(d);
     for (int k = 0; k < n; ++k) {
         if (d->stg.on) {
-            // U(t) of the inflow faces; with a held stride only at anchors
-            const StgState &s = d->stg;
-            if (!s.valid || s.p.interpolate || d->t % s.p.stride == 0) {
-                lbm_status st = cuda_check(d, launch_stg(s, d->t, d->stream), "stg kernel launch");
+            // U of the inflow faces, evaluated only at anchors t_a = floor(t/s) s: held, or (stride
+            // > 1 with interpolation) kept for t_a and t_a + s and blended by the step itself
+            StgState &s = d->stg;
+            const long long t = d->t, sp = s.p.stride, ta = (t / sp) * sp;
+            const bool interp = s.p.interpolate && sp > 1;
+            if (!s.valid || s.anchor != ta) {
+                cudaError_t e;
+                if (interp && s.valid && s.anchor == ta - sp) {
+                    s.cur ^= 1;                             // U(t_a) was the previous "next"
+                    e = launch_stg(s, ta + sp, 1 - s.cur, d->stream);
+                } else {
+                    e = launch_stg(s, ta, s.cur, d->stream);
+                    if (e == cudaSuccess && interp) e = launch_stg(s, ta + sp, 1 - s.cur, d->stream);
+                }
+                lbm_status st = cuda_check(d, e, "stg kernel launch");
                 if (st != LBM_OK) return st;
+                s.anchor = ta;
+                s.valid = true;
             }
-            d->stg.valid = true;
+            s.alpha = interp ? (float)(t - ta) / (float)sp : 0.0f;
         }
         const StepArgs a = args_of(d);
         launch_step(d->p.store, (d->t & 1) == 0, force, a, d->stream);

@@ -182,9 +182,11 @@ struct StepArgs {
     int pack16;                 // 16-bit storage with N and nx even: lattice blocks update pairs of
                                 // adjacent cells with 4-byte accesses
     const float4 *ueq[6];       // synthetic inflow turbulence (App. F): per inflow face x-, x+, y-,
-                                // y+, z+ the velocity of its equilibrium cells, [n2][n1] in the
-                                // face's plane (x+- : y + ny z; y+- : x + nx z; z+ : x + nx y);
-                                // all null = the equilibrium cells take u_b(z)
+                                // y+, z+ the velocity of its equilibrium cells at the current
+                                // anchor, [n2][n1] in the face's plane (x+- : y + ny z;
+                                // y+- : x + nx z; z+ : x + nx y); all null = u_b(z)
+    const float4 *ueq_next[6];  // the same at the next anchor (used when ueq_alpha != 0)
+    float ueq_alpha;            // U = (1 - alpha) ueq + alpha ueq_next
 };
 
 // The z face layers whose cells (with interior x and y) take the layer path: no-slip or free-slip
@@ -559,15 +561,23 @@ LBM_HD void cell_coords(const Geo &G, long long n, int &x, int &y, int &z) {
 // inflow ground) and every cell without turbulence take the profile u_b(z).
 LBM_HD void eq_velocity(const StepArgs &a, int x, int y, int z, float &ux, float &uy, float &uz) {
     const Geo &G = a.g;
-    const float4 *p = nullptr;
-    if (a.ueq[0] && x == 0) p = a.ueq[0] + y + (long long)G.ny * z;
-    else if (a.ueq[1] && x == G.nx - 1) p = a.ueq[1] + y + (long long)G.ny * z;
-    else if (a.ueq[2] && y == 0) p = a.ueq[2] + x + (long long)G.nx * z;
-    else if (a.ueq[3] && y == G.ny - 1) p = a.ueq[3] + x + (long long)G.nx * z;
-    else if (a.ueq[5] && z == G.nz - 1) p = a.ueq[5] + x + (long long)G.nx * y;
-    if (p) {
-        const float4 v = *p;
+    int k = -1;
+    long long idx = 0;
+    if (a.ueq[0] && x == 0) { k = 0; idx = y + (long long)G.ny * z; }
+    else if (a.ueq[1] && x == G.nx - 1) { k = 1; idx = y + (long long)G.ny * z; }
+    else if (a.ueq[2] && y == 0) { k = 2; idx = x + (long long)G.nx * z; }
+    else if (a.ueq[3] && y == G.ny - 1) { k = 3; idx = x + (long long)G.nx * z; }
+    else if (a.ueq[5] && z == G.nz - 1) { k = 5; idx = x + (long long)G.nx * y; }
+    if (k >= 0) {
+        const float4 v = a.ueq[k][idx];
         ux = v.x; uy = v.y; uz = v.z;
+        if (a.ueq_alpha != 0.0f) {   // linear in time between two anchors (App. F, stride s)
+            const float4 w = a.ueq_next[k][idx];
+            const float al = a.ueq_alpha;
+            ux = (1.0f - al) * ux + al * w.x;
+            uy = (1.0f - al) * uy + al * w.y;
+            uz = (1.0f - al) * uz + al * w.z;
+        }
     } else {
         ux = a.ub[3 * z]; uy = a.ub[3 * z + 1]; uz = a.ub[3 * z + 2];
     }

@@ -39,75 +39,135 @@ LBM_HD int owner_face(int inflow, const Geo &g, int x, int y, int z) {
     return -1;
 }
 
-// Time coefficients of entry e = 3 m + a: A_m,a (cos, sin) of the mode's phase at the anchor(s).
-LBM_HD void stg_coeff(const StgLaunch &L, const StgFace &F, float *cs, int e) {
-    const int m = e / 3, c = e - 3 * m;
+// Time coefficients of mode m at the launch's time t: A_m,a (cos, sin) of the phases, stored as
+// two float4 (C_x, C_y, C_z, S_x), (S_y, S_z, -, -).  omega_m t is reduced to turns in FP64 once per
+// mode; the per-component phase offsets are added in FP32 within [0, 2).
+LBM_HD void stg_coeff(const StgLaunch &L, const StgFace &F, float4 *cs, int m) {
     const StgMode &M = F.mode[m];
-    const long long ta = (L.t / L.stride) * L.stride;
-    float C = 0.0f, S = 0.0f;
-    const int nt = (L.interpolate && L.t != ta) ? 2 : 1;
-    const float alpha = (float)(L.t - ta) / (float)L.stride;
-    for (int r = 0; r < nt; ++r) {
-        double th = M.w * (double)(ta + r * L.stride) + M.ph[c];
-        th -= floor(th);                                    // turns, in [0, 1)
-        float sv, cv;
+    double tw = M.w * (double)L.t;
+    tw -= floor(tw);                                        // turns, in [0, 1)
+    float C[3], S[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float th = (float)tw + M.ph[c];               // in [0, 2)
 #ifdef __CUDA_ARCH__
-        sincospif(2.0f * (float)th, &sv, &cv);
+        sincospif(2.0f * th, &S[c], &C[c]);
 #else
-        sv = (float)sin(2.0 * kPi * th); cv = (float)cos(2.0 * kPi * th);
+        S[c] = (float)sin(2.0 * kPi * th); C[c] = (float)cos(2.0 * kPi * th);
 #endif
-        const float wgt = nt == 1 ? 1.0f : (r == 0 ? 1.0f - alpha : alpha);
-        C += wgt * cv;
-        S += wgt * sv;
     }
-    cs[6 * m + c] = M.amp[c] * C;
-    cs[6 * m + 3 + c] = M.amp[c] * S;
+    cs[2 * m] = make_float4(M.amp[0] * C[0], M.amp[1] * C[1], M.amp[2] * C[2], M.amp[0] * S[0]);
+    cs[2 * m + 1] = make_float4(M.amp[1] * S[1], M.amp[2] * S[2], 0.0f, 0.0f);
 }
 
-// U_i(t) of the cell at position pos of face F (nothing for a position another face owns or a
-// solid one).
-LBM_HD void stg_cell(const StgLaunch &L, const StgFace &F, const float *cs, long long pos) {
-    const int i = (int)(pos % F.n1), j = (int)(pos / F.n1);
+// Whether the position pos of face F is an equilibrium cell this face owns (else nothing is
+// written there); if so its plane coordinates, u_b and, when it is turbulent, sigma_i.
+LBM_HD bool stg_target(const StgLaunch &L, const StgFace &F, int pos, int &i, int &j, float4 &ub,
+                       float &sigma, bool &turb) {
+    j = pos / F.n1;
+    i = pos - j * F.n1;
+    turb = false;
+    if (j >= F.n2) return false;
     int x, y, z;
     face_pos(L.g, F.face, i, j, x, y, z);
-    if (owner_face(L.inflow, L.g, x, y, z) != F.face) return;
-    if (!(L.flags[cell_of(L.g, x, y, z)] & F_EQ)) return;
+    if (owner_face(L.inflow, L.g, x, y, z) != F.face) return false;
+    if (!(L.flags[cell_of(L.g, x, y, z)] & F_EQ)) return false;
     const float bx = L.ub[3 * z], by = L.ub[3 * z + 1], bz = L.ub[3 * z + 2];
-    float4 out = make_float4(bx, by, bz, 0.0f);
+    ub = make_float4(bx, by, bz, 0.0f);
     const int a = F.face / 2;
     const float ua = a == 0 ? bx : (a == 1 ? by : bz);
     const float un = (F.face & 1) ? -ua : ua;               // U_b . n_f, n_f the inward normal
     if (F.keep && !(L.inflow_only && !(un > 0.0f))) {
+        turb = true;
         const float uchar = L.char_normal ? fabsf(un) : sqrtf(bx * bx + by * by + bz * bz);
-        const float sigma = L.intensity > 0.0f ? L.intensity * uchar : L.sigma0;
-        float qx = 0.0f, qy = 0.0f, qz = 0.0f;
-        const float2 *e1 = F.E1 + i, *e2 = F.E2 + j;
-        for (int m = 0; m < L.n_modes; ++m) {
-            const float2 p = e1[(long long)m * F.n1], q = e2[(long long)m * F.n2];
-            const float re = p.x * q.x - p.y * q.y, im = p.x * q.y + p.y * q.x;
-            const float *k = cs + 6 * m;
-            qx += k[0] * re - k[3] * im;
-            qy += k[1] * re - k[4] * im;
-            qz += k[2] * re - k[5] * im;
-        }
-        out.x += sigma * qx;
-        out.y += sigma * qy;
-        out.z += sigma * qz;
+        sigma = L.intensity > 0.0f ? L.intensity * uchar : L.sigma0;
     }
-    F.ueq[pos] = out;
+    return true;
 }
 
+#ifdef __CUDA_ARCH__
+#define STG_LD(p) __ldg(p)
+#else
+#define STG_LD(p) (*(p))
+#endif
+
+// Partial mode sum over m = m0, m0 + dm, ... at plane position (i, j).  The table loads of
+// kStgBatch modes are issued together (one memory round trip per batch: the tables are evicted
+// from L2 by every lattice step, so each launch reads them from DRAM).
+LBM_HD void stg_partial(const StgFace &F, const float4 *cs, int n_modes, int i, int j, int m0, int dm,
+                        float &qx, float &qy, float &qz) {
+    const float2 *__restrict__ e1 = F.E1 + i + m0 * F.n1;
+    const float2 *__restrict__ e2 = F.E2 + j + m0 * F.n2;
+    const int s1 = dm * F.n1, s2 = dm * F.n2;
+    for (int mb = m0; mb < n_modes; mb += kStgBatch * dm) {
+        float2 p[kStgBatch], q[kStgBatch];
+#pragma unroll
+        for (int u = 0; u < kStgBatch; ++u) {
+            if (mb + u * dm < n_modes) {
+                p[u] = STG_LD(e1 + u * s1);
+                q[u] = STG_LD(e2 + u * s2);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kStgBatch; ++u) {
+            const int m = mb + u * dm;
+            if (m < n_modes) {
+                const float re = p[u].x * q[u].x - p[u].y * q[u].y;
+                const float im = p[u].x * q[u].y + p[u].y * q[u].x;
+                const float4 a = cs[2 * m], b = cs[2 * m + 1];
+                qx += a.x * re - a.w * im;
+                qy += a.y * re - b.x * im;
+                qz += a.z * re - b.y * im;
+            }
+        }
+        e1 += kStgBatch * s1;
+        e2 += kStgBatch * s2;
+    }
+}
+
+// A block updates kStgPos plane positions of one face; its kStgGroups thread groups split the
+// modes (the faces hold only ~1e5 cells, so mode parallelism is what fills the GPU) and add their
+// partial sums through shared memory.  The cell's flag and profile loads are issued before the
+// time coefficients are computed, so both memory round trips overlap.
 __global__ void __launch_bounds__(kStgBlock) k_stg(const StgLaunch L) {
-    __shared__ float cs[kStgMaxModes * 6];
+    __shared__ float4 cs[kStgMaxModes * 2];
+    __shared__ float red[kStgGroups - 1][3][kStgPos];
     int fi = 0;
     for (int k = 1; k < L.nfaces; ++k)
         if ((int)blockIdx.x >= L.f[k].block_begin) fi = k;
     const StgFace &F = L.f[fi];
+    const int pl = threadIdx.x % kStgPos, grp = threadIdx.x / kStgPos;
+    const int pos = ((int)blockIdx.x - F.block_begin) * kStgPos + pl;
+    int i, j;
+    float4 ub;
+    float sigma = 0.0f;
+    bool turb;
+    const bool target = stg_target(L, F, pos, i, j, ub, sigma, turb);
     if (F.keep)
-        for (int e = threadIdx.x; e < 3 * L.n_modes; e += kStgBlock) stg_coeff(L, F, cs, e);
+        for (int m = threadIdx.x; m < L.n_modes; m += kStgBlock) stg_coeff(L, F, cs, m);
     __syncthreads();
-    const long long pos = (long long)(blockIdx.x - F.block_begin) * kStgBlock + threadIdx.x;
-    if (pos < (long long)F.n1 * F.n2) stg_cell(L, F, cs, pos);
+    float qx = 0.0f, qy = 0.0f, qz = 0.0f;
+    if (target && turb) stg_partial(F, cs, L.n_modes, i, j, grp, kStgGroups, qx, qy, qz);
+    if (grp > 0) {
+        red[grp - 1][0][pl] = qx;
+        red[grp - 1][1][pl] = qy;
+        red[grp - 1][2][pl] = qz;
+    }
+    __syncthreads();
+    if (grp == 0 && target) {
+#pragma unroll
+        for (int g = 0; g < kStgGroups - 1; ++g) {
+            qx += red[g][0][pl];
+            qy += red[g][1][pl];
+            qz += red[g][2][pl];
+        }
+        if (turb) {
+            ub.x += sigma * qx;
+            ub.y += sigma * qy;
+            ub.z += sigma * qz;
+        }
+        F.ueq[pos] = ub;
+    }
 }
 
 }  // namespace
@@ -124,7 +184,7 @@ size_t stg_workspace_bytes(const Geo &g, int n_modes) {
                   al((size_t)n_modes * sizeof(StgMode));
         planes += al((size_t)n1 * n2 * sizeof(float4));
     }
-    return tables + planes;
+    return tables + 2 * planes;
 }
 
 const char *stg_check(const lbm_stg_params *p) {
@@ -199,7 +259,7 @@ const char *stg_build(StgState &s, const Geo &g, const float *ub, const std::vec
 
     // workspace image: per inflow face E1, E2, modes; then the velocity planes
     size_t off = 0;
-    struct Reg { size_t e1, e2, mode, plane; int n1, n2; } reg[6] = {};
+    struct Reg { size_t e1, e2, mode, plane[2]; int n1, n2; } reg[6] = {};
     for (int k : kOrder) {
         if (!(inflow & (1 << k))) continue;
         stg_face_dims(g, k, reg[k].n1, reg[k].n2);
@@ -208,10 +268,11 @@ const char *stg_build(StgState &s, const Geo &g, const float *ub, const std::vec
         reg[k].mode = off; off += al((size_t)Nm * sizeof(StgMode));
     }
     s.table_bytes = off;
-    for (int k : kOrder) {
-        if (!(inflow & (1 << k))) continue;
-        reg[k].plane = off; off += al((size_t)reg[k].n1 * reg[k].n2 * sizeof(float4));
-    }
+    for (int b = 0; b < 2; ++b)
+        for (int k : kOrder) {
+            if (!(inflow & (1 << k))) continue;
+            reg[k].plane[b] = off; off += al((size_t)reg[k].n1 * reg[k].n2 * sizeof(float4));
+        }
     if (off > s.ws_bytes) return "stg: workspace too small";
     s.image.assign(s.table_bytes, 0);
 
@@ -234,9 +295,11 @@ const char *stg_build(StgState &s, const Geo &g, const float *ub, const std::vec
         F.E1 = (const float2 *)(s.ws + reg[k].e1);
         F.E2 = (const float2 *)(s.ws + reg[k].e2);
         F.mode = (const StgMode *)(s.ws + reg[k].mode);
-        F.ueq = (float4 *)(s.ws + reg[k].plane);
+        s.plane[0][L.nfaces - 1] = (float4 *)(s.ws + reg[k].plane[0]);
+        s.plane[1][L.nfaces - 1] = (float4 *)(s.ws + reg[k].plane[1]);
+        F.ueq = s.plane[0][L.nfaces - 1];
         F.block_begin = blocks;
-        blocks += (int)(((long long)F.n1 * F.n2 + kStgBlock - 1) / kStgBlock);
+        blocks += (int)(((long long)F.n1 * F.n2 + kStgPos - 1) / kStgPos);
         if (!F.keep) continue;
         // modes of this face: log-spaced band, isotropic directions, von Karman weights
         double suma2 = 0.0;
@@ -268,10 +331,9 @@ const char *stg_build(StgState &s, const Geo &g, const float *ub, const std::vec
             for (int c = 0; c < 3; ++c) {
                 double ph = kk[a] * xf / (2.0 * kPi) + R[3 + c];
                 ph -= std::floor(ph);
-                M[m].ph[c] = ph;
+                M[m].ph[c] = (float)ph < 1.0f ? (float)ph : 0.0f;
                 M[m].amp[c] = (float)(s.p.gain[c] * amp[m] / norm);
             }
-            M[m].pad = 0.0f;
             for (int i = 0; i < reg[k].n1; ++i) {
                 const double p = kk[a1] * i;
                 E1[(size_t)m * reg[k].n1 + i] = make_float2((float)std::cos(p), (float)std::sin(p));
@@ -284,8 +346,6 @@ const char *stg_build(StgState &s, const Geo &g, const float *ub, const std::vec
     }
     L.nblocks = blocks;
     L.n_modes = Nm;
-    L.stride = s.p.stride;
-    L.interpolate = s.p.interpolate ? 1 : 0;
     L.char_normal = cn ? 1 : 0;
     L.inflow_only = io ? 1 : 0;
     L.intensity = s.p.intensity;
@@ -297,9 +357,10 @@ const char *stg_build(StgState &s, const Geo &g, const float *ub, const std::vec
     return nullptr;
 }
 
-cudaError_t launch_stg(const StgState &s, long long t, cudaStream_t st) {
+cudaError_t launch_stg(const StgState &s, long long t, int buf, cudaStream_t st) {
     StgLaunch L = s.L;
     L.t = t;
+    for (int k = 0; k < L.nfaces; ++k) L.f[k].ueq = s.plane[buf][k];
     if (L.nblocks <= 0) return cudaSuccess;
     k_stg<<<L.nblocks, kStgBlock, 0, st>>>(L);
     return cudaGetLastError();
