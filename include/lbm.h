@@ -98,9 +98,10 @@ lbm_status lbm_coriolis_omega(double lat_deg, double dt_si, float *out);
 lbm_status lbm_faces_for_direction(float theta, int *face);
 
 /* Bytes of device workspace a domain of this size and storage needs (0 if the arguments are
- * invalid).  Layout (all regions 256-byte aligned): populations 19 * N * sizeof(store),
- * cell flags N bytes, inflow profile nz * 3 floats, exit buffers for outflow faces, reduction
- * scratch. */
+ * invalid).  Layout (all regions 256-byte aligned): populations 19 * N * sizeof(store) between
+ * two guard regions, cell flags N bytes, cell info 4 N bytes, inflow profile nz * 3 floats, exit
+ * buffers for outflow faces, precomputed boundary tables of the face cells (58 * 4 bytes per
+ * face cell; omitted above 2^30 cells), reduction scratch. */
 size_t lbm_workspace_bytes(int nx, int ny, int nz, const lbm_params *p);
 
 /* Create a domain in the caller's workspace.

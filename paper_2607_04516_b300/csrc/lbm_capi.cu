@@ -25,8 +25,9 @@ size_t store_bytes(int store) { return store == LBM_F32 ? 4 : 2; }
 
 // Regions of the caller's workspace, in bytes from its start.
 struct Layout {
-    size_t f, flags, info, ub, side[6], part, diag, total;
+    size_t f, flags, info, ub, side[6], ftab, part, diag, total;
     long long side_cells[6];
+    int ngen;   // face cells with precomputed tables (0: none)
 };
 
 bool valid_face(int k) { return k >= LBM_FACE_PERIODIC && k <= LBM_FACE_NOSLIP; }
@@ -81,6 +82,17 @@ Layout make_layout(int nx, int ny, int nz, const lbm_params *p) {
             off = align_up(off + (size_t)Q * fc[k / 2] * sb);
         }
     }
+    // face tables of every face cell; their element codes are 32-bit offsets from the population
+    // base and their heads hold 30-bit cell indices, so the populations and side buffers must span
+    // fewer than 2^32 - 1 storage elements and the lattice fewer than 2^30 cells (else the face
+    // blocks resolve every boundary rule at run time)
+    Geo g{};
+    g.N = N; g.nx = nx; g.ny = ny; g.nz = nz; g.sy = nx; g.sz = (long long)nx * ny;
+    for (int k = 0; k < 6; ++k) g.face[k] = p->face[k];
+    const long long ngen = face_cell_count(g);
+    const bool fits = (off - L.f) / sb < (size_t)0xffffffffu && N <= (long long)kFtCell;
+    L.ngen = fits ? (int)ngen : 0;
+    L.ftab = off; off = align_up(off + (size_t)L.ngen * kFtWords * sizeof(uint32_t));
     L.part = off; off = align_up(off + (size_t)kRedBlocks * 4 * sizeof(double));
     L.diag = off; off = align_up(off + 4 * sizeof(double));
     L.total = off;
@@ -149,6 +161,8 @@ StepArgs args_of(const lbm_domain *d) {
     a.zface_begin = xs * d->ny * d->nz + ys * ix * d->nz;
     a.zfast = zfast_mask(a.g);
     a.pack16 = (d->p.store != LBM_F32 && d->N % 2 == 0 && d->nx % 2 == 0) ? 1 : 0;
+    a.ftab = d->L.ngen ? (const uint32_t *)(d->ws + d->L.ftab) : nullptr;
+    a.ngen = d->L.ngen;
     if (d->stg.on && d->stg.valid) {
         const StgState &s = d->stg;
         for (int k = 0; k < s.L.nfaces; ++k) {
@@ -281,6 +295,8 @@ lbm_status lbm_create_domain(const uint8_t *solid, int nx, int ny, int nz, const
     for (int k = 0; k < 6 && st == LBM_OK; ++k)
         if (L.side_cells[k])
             st = cuda_check(d, cudaMemsetAsync(d->ws + L.side[k], 0, (size_t)Q * L.side_cells[k] * store_bytes(p->store), d->stream), "side buffer clear");
+    if (st == LBM_OK && L.ngen)
+        st = cuda_check(d, launch_face_tables(p->store, a, (uint32_t *)(d->ws + L.ftab), d->stream), "face table kernel");
     if (st == LBM_OK) st = cuda_check(d, launch_init(p->store, a, nullptr, nullptr, d->stream), "init kernel");
     if (st != LBM_OK) {
         delete d;

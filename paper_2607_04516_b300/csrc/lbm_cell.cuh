@@ -250,6 +250,99 @@ LBM_HD void cell_neighbor_face(const StepArgs &a, uint8_t fl, int x, int y, int 
     }
 }
 
+// ---------------------------------------------------------------- face tables
+// The boundary resolution of a face cell depends only on the geometry and the solid mask, so it is
+// done once, at domain creation, for the face cells [0, ngen) of the face enumeration: per cell its
+// index and kind, per direction the storage element (offset from the population base, in storage
+// elements; the side buffers lie after it in the workspace) its gather reads, and up to two
+// elements its scatter writes.
+//   tab[t]                         kFtNone for a solid cell, else the cell index | kFtEq for an
+//                                  equilibrium cell | kFtGeneral when some direction has more
+//                                  than two scatter targets (the cell keeps the general resolution)
+//   tab[(1 + i) ngen + t]          gather element of direction i (fluid cells)
+//   tab[(20 + j) ngen + t]         first scatter element of direction j (kFtNone: none)
+//   tab[(39 + j) ngen + t]         second scatter element (kFtNone: none)
+
+template <int S>
+LBM_HD void cell_face_table(const StepArgs &a, int t, uint32_t *__restrict__ tab) {
+    using T = typename Codec<S>::T;
+    const long long ng = a.ngen;
+    int x, y, z;
+    face_cell_xyz(a.g, t, x, y, z);
+    const long long n = cell_of(a.g, x, y, z);
+    const uint8_t fl = a.flags[n];
+    uint32_t head = (uint32_t)n | ((fl & F_EQ) ? kFtEq : 0u);
+    long long sbase[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        sbase[k] = a.side[k] ? (long long)(((const char *)a.side[k] - (const char *)a.f) / (long long)sizeof(T)) : 0;
+    const auto code = [&](int kind, long long idx) -> uint32_t {
+        return (uint32_t)(kind == 0 ? idx : sbase[kind - 1] + idx);
+    };
+    // a layer cell with solid neighbours follows the store-side bounce-back convention of the
+    // lattice (its local step parks the reflected population in the solid neighbour's slot), so a
+    // gather from a solid neighbour x - c_i is the plain pull from that neighbour
+    const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
+    for (int i = 0; i < Q; ++i) {
+        uint32_t gv = kFtNone;
+        if (!(fl & (F_SOLID | F_EQ))) {
+            const Loc l = ((nb >> opp_rt(i)) & 1u) ? Loc{0, (long long)opp_rt(i) * a.g.N + n - a.off[i]}
+                                                  : gather_loc_B(a.g, a.flags, x, y, z, i);
+            gv = code(l.kind, l.idx);
+        }
+        tab[(1 + i) * ng + t] = gv;
+    }
+    const bool fluid = !(fl & F_EQ);
+    for (int j = 0; j < Q; ++j) {
+        uint32_t v[2] = {kFtNone, kFtNone};
+        int cnt = 0;
+        if (!(fl & F_SOLID))
+            scatter_targets(a.g, a.flags, x, y, z, j, fluid, [&](int kind, long long idx) {
+                if (cnt < 2) v[cnt] = code(kind, idx);
+                ++cnt;
+            });
+        if (cnt > 2) head |= kFtGeneral;
+        tab[(1 + Q + j) * ng + t] = v[0];
+        tab[(1 + 2 * Q + j) * ng + t] = v[1];
+    }
+    tab[t] = (fl & F_SOLID) ? kFtNone : head;
+}
+
+// Face cell t of the tables: gathers and scatters through the precomputed elements.  The head and
+// the gather elements are loaded together (they depend on t only), so a fluid cell waits for two
+// memory round trips before its collision.  Returns false (nothing done) for a cell that keeps the
+// general resolution.
+template <int S, bool FORCE>
+LBM_HD bool cell_neighbor_table(const StepArgs &a, int t) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    T *__restrict__ f = (T *)a.f;
+    const uint32_t *__restrict__ tab = a.ftab;
+    const long long ng = a.ngen;
+    uint32_t e[Q];
+    const uint32_t head = tab[t];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) e[i] = tab[(1 + i) * ng + t];
+    if (head == kFtNone) return true;   // solid
+    if (head & kFtGeneral) return false;
+    float g[Q];
+    if (head & kFtEq) {
+        eq_cell_g(a, (long long)(head & kFtCell), g);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = Cd::dec(f[e[i]]);
+        collide<FORCE>(g, a);
+    }
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const T v = Cd::enc(g[j]);
+        const uint32_t e0 = tab[(1 + Q + j) * ng + t], e1 = tab[(1 + 2 * Q + j) * ng + t];
+        if (e0 != kFtNone) f[e0] = v;
+        if (e1 != kFtNone) f[e1] = v;
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------- two cells per thread (16-bit)
 // With 2-byte populations one cell per thread leaves too few bytes in flight; a thread updates
 // the cells n0 and n1 = n0 + 256 (so every warp access stays 32 consecutive cells), issuing the

@@ -187,7 +187,16 @@ struct StepArgs {
                                 // y+- : x + nx z; z+ : x + nx y); all null = u_b(z)
     const float4 *ueq_next[6];  // the same at the next anchor (used when ueq_alpha != 0)
     float ueq_alpha;            // U = (1 - alpha) ueq + alpha ueq_next
+    const uint32_t *ftab;       // face tables of the first ngen face cells (null: every face cell
+    int ngen;                   // takes the general resolution); layout in lbm_cell.cuh
 };
+
+// Face tables (see cell_face_table): 32-bit storage-element codes per face cell
+constexpr uint32_t kFtNone = 0xffffffffu;      // no element (head: a solid cell)
+constexpr uint32_t kFtGeneral = 0x80000000u;   // head bit: the cell keeps the general resolution
+constexpr uint32_t kFtEq = 0x40000000u;        // head bit: an equilibrium cell
+constexpr uint32_t kFtCell = 0x3fffffffu;      // head bits of the cell index
+constexpr int kFtWords = 1 + 3 * Q;            // words per face cell
 
 // The z face layers whose cells (with interior x and y) take the layer path: no-slip or free-slip
 // faces on a lattice at least 3 x 3 x 2.

@@ -19,6 +19,7 @@ cudaError_t launch_sample(int store, const StepArgs &a, bool layoutA, const int 
 cudaError_t launch_export(int store, const StepArgs &a, bool layoutA, float *out, cudaStream_t s);
 cudaError_t launch_reduce(int store, const StepArgs &a, bool layoutA, double *part, double *out,
                           cudaStream_t s);
+cudaError_t launch_face_tables(int store, const StepArgs &a, uint32_t *tab, cudaStream_t s);
 
 // Read-only view of a domain for entry points defined outside lbm_capi.cu.
 struct DomainView {

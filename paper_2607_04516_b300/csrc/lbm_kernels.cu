@@ -87,6 +87,13 @@ __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_NEIGHBOR) k_step_neighb
         const long long t = (long long)blockIdx.x * kBlock + threadIdx.x;
         if (t >= a.nface) return;
         int x, y, z;
+        if (a.ftab) {   // tables cover every face cell
+            if (cell_neighbor_table<S, FORCE>(a, (int)t)) return;
+            const int n = (int)(a.ftab[t] & kFtCell);
+            cell_coords(a.g, n, x, y, z);
+            cell_neighbor_face<S, FORCE>(a, a.flags[n], x, y, z);
+            return;
+        }
         face_cell_xyz(a.g, t, x, y, z);
         const int n = (int)cell_of(a.g, x, y, z);
         const uint8_t fl = a.flags[n];
@@ -97,6 +104,15 @@ __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_NEIGHBOR) k_step_neighb
         }
         cell_neighbor_face<S, FORCE>(a, fl, x, y, z);
     }
+}
+
+// Face tables (once per domain, after the flags; without them, as on lattices too large for their
+// 32-bit codes, the face blocks resolve the boundary rules at run time).
+template <int S>
+__global__ void k_face_tables(StepArgs a, uint32_t *__restrict__ tab) {
+    const long long t = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (t >= a.ngen) return;
+    cell_face_table<S>(a, (int)t, tab);
 }
 
 template <int S>
@@ -266,6 +282,20 @@ void launch_step(int store, bool neighbor, bool force, const StepArgs &a, cudaSt
         case LBM_F32: step_s<LBM_F32>(neighbor, force, a, s); break;
         case LBM_F16S: step_s<LBM_F16S>(neighbor, force, a, s); break;
         default: step_s<LBM_BF16S>(neighbor, force, a, s); break;
+    }
+}
+
+template <int S>
+static cudaError_t face_tables_t(const StepArgs &a, uint32_t *tab, cudaStream_t s) {
+    if (a.ngen <= 0) return cudaSuccess;
+    k_face_tables<S><<<blocks_for(a.ngen), kBlock, 0, s>>>(a, tab);
+    return cudaGetLastError();
+}
+cudaError_t launch_face_tables(int store, const StepArgs &a, uint32_t *tab, cudaStream_t s) {
+    switch (store) {
+        case LBM_F32: return face_tables_t<LBM_F32>(a, tab, s);
+        case LBM_F16S: return face_tables_t<LBM_F16S>(a, tab, s);
+        default: return face_tables_t<LBM_BF16S>(a, tab, s);
     }
 }
 
