@@ -236,3 +236,69 @@ def stg_uniforms(n_modes: int, seed: int, shared: bool = False) -> np.ndarray:
         rng = np.random.default_rng([seed, 0 if shared else f + 1])
         out[f] = rng.random((n_modes, 6))
     return out
+
+
+# ----------------------------------------------------------------------------- boundary assimilation
+def lidar_columns(solid: np.ndarray, n_cols: int, seed: int, clearance: int = 3,
+                  top: int | None = None, face_margin: int = 10) -> np.ndarray:
+    """(n_cols, 2) integer (x, y) positions of virtual lidar columns, drawn uniformly (PCG64
+    stream ``seed``) among the columns whose cells up to height ``top`` (default: all) are at
+    least ``clearance`` cells (Chebyshev distance) from every solid cell and at least
+    ``face_margin`` cells from the lateral faces (inside the built-up area); distinct columns."""
+    nz, ny, nx = solid.shape
+    top = nz if top is None else top
+    blocked = solid[:top].any(axis=0)
+    ok = np.zeros((ny, nx), bool)
+    m = max(clearance, face_margin)
+    ok[m:ny - m, m:nx - m] = True
+    ys, xs = np.nonzero(blocked)
+    for y, x in zip(ys, xs):
+        ok[max(0, y - clearance):y + clearance + 1, max(0, x - clearance):x + clearance + 1] = False
+    cand = np.argwhere(ok)                      # (m, 2) = (y, x)
+    if len(cand) < n_cols:
+        raise ValueError("not enough clear columns")
+    pick = np.random.default_rng(seed).choice(len(cand), size=n_cols, replace=False)
+    return np.stack([cand[pick, 1], cand[pick, 0]], axis=1).astype(np.int32)
+
+
+@dataclass
+class Assimilation:
+    """Inflow recovery from virtual lidar: a city, hidden 'truth' inflow parameters, a first
+    guess, the lidar columns and heights, and the averaging window."""
+    case: Case
+    L: int                       # level speeds
+    speed_true: np.ndarray
+    theta_true: float
+    speed_guess: np.ndarray
+    theta_guess: float
+    cols: np.ndarray             # (ncol, 2) int32 (x, y)
+    heights: np.ndarray          # (nh,) int32 cell heights
+    nsteps: int
+    n_avg: int                   # the last n_avg states of the run are averaged
+    checkpoint_every: int
+
+
+def assimilation_case(nx: int = 128, ny: int = 128, nz: int = 48, seed: int = 4, L: int = 24,
+                      n_cols: int = 8, heights=tuple(range(4, 41, 4)), nsteps: int = 2000,
+                      n_avg: int = 500, checkpoint_every: int = 100, tau: float = 0.505,
+                      cs: float = 0.16, u_ref: float = 0.06, z_ref: float = 60.0,
+                      alpha: float = 0.25, guess_scale: float = 0.8,
+                      guess_dtheta: float = 0.1) -> Assimilation:
+    """Synthetic city (same generator as ``city_case``, seed-fixed) whose inflow is parameterised
+    by L level speeds (equal blocks of nz / L cells) and one direction.  Truth: the power law at
+    the level centres from a seeded direction; first guess: ``guess_scale`` x the truth speeds and
+    the direction turned by ``guess_dtheta`` rad (the face kinds follow the truth direction and
+    stay fixed).  Lidar columns: ``n_cols`` seeded fluid columns >= 2 cells from solids and
+    >= 10 cells from the lateral faces (at a plan-area fraction of 0.35 only a handful of columns
+    inside the built-up area keep 3 cells from every building)."""
+    solid, info = city_mask(nx, ny, nz, seed)
+    theta = direction_from_seed(seed)
+    zc = (np.arange(L) + 0.5) * nz / L
+    speed = u_ref * (zc / z_ref) ** alpha
+    faces = faces_for_direction(theta)
+    heights = np.asarray(heights, np.int32)
+    cols = lidar_columns(solid, n_cols, seed + 7, clearance=2, top=int(heights.max()) + 1)
+    case = Case(f"assim{nx}x{ny}x{nz}", solid, faces, tau, cs, speed, theta,
+                meta={"seed": seed, **info})
+    return Assimilation(case, L, speed, theta, guess_scale * speed, theta + guess_dtheta, cols,
+                        heights, nsteps, n_avg, checkpoint_every)
