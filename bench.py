@@ -36,7 +36,7 @@ WORKLOADS = {
     "city1000": dict(nx=1000, ny=1000, nz=160, seed=1),
     "cube": None,
 }
-METRIC = "LBM-LES GLUPS & % HBM roofline, FP32 vs 16-bit storage"
+METRIC = "LBM-LES GLUPS & % HBM roofline, FP32 vs 16-bit storage; adjoint/forward time ratio"
 STORE_BYTES = {"f32": 4, "f16s": 2, "bf16s": 2}
 DTYPE_NAME = {"f32": "f32", "f16s": "f16-storage/f32-math", "bf16s": "bf16-storage/f32-math"}
 SOURCES = ["paper_2607_04516_b300/csrc/lbm_device.cuh", "paper_2607_04516_b300/csrc/lbm_cell.cuh",
@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--store", default="f32", choices=list(STORE_BYTES))
     ap.add_argument("--workload", default="city400", choices=list(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10",
+    ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10,adjoint",
                     help="extra storage kinds timed after the main measurement ('' = none)")
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -241,6 +241,70 @@ def e2e_glups(dom, case, steps: int, world: int):
             dt * 1e3 / steps)
 
 
+def adjoint_leg(world: int):
+    """Boundary assimilation (128 x 128 x 48 city, 24 level speeds + direction, 8 lidar columns x
+    10 heights averaged over the last 500 of 2000 steps, checkpoints every 100 steps): time of the
+    misfit gradient (forward run + reverse sweep, lbm_lidar_misfit_grad) against 2000 plain FP32
+    steps of the same lattice (lbm_step), both with CUDA events on the domain's stream."""
+    import numpy as np
+    import torch
+    from paper_2607_04516_b300 import lbm, synth
+    a = synth.assimilation_case()
+    c = a.case
+    dom = lbm.Domain(c.solid, c.faces, c.tau, c.cs, "f32")
+    prob = lbm.LidarProblem(dom, a.cols, a.heights, np.zeros((len(a.cols), len(a.heights), 2), np.float32),
+                            a.nsteps, a.n_avg, a.checkpoint_every)
+    _, mean = prob.misfit(a.speed_true.astype(np.float32), a.theta_true, target=False)
+    prob.target = mean[..., :2].float().contiguous()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    guess = a.speed_guess.astype(np.float32)
+    prob.misfit_grad(guess, a.theta_guess)                   # warm-up (allocates the workspace)
+    dom.set_inflow_profile(guess, a.theta_guess)
+    dom.init_fields()
+    dom.step(20)
+    torch.cuda.synchronize()
+    barrier(world)
+    ev[0].record(dom.stream)
+    dom.step(a.nsteps)
+    ev[1].record(dom.stream)
+    ev[2].record(dom.stream)
+    J0, _ = prob.misfit(guess, a.theta_guess)
+    ev[3].record(dom.stream)
+    ev[4].record(dom.stream)
+    J, g, _ = prob.misfit_grad(guess, a.theta_guess)
+    ev[5].record(dom.stream)
+    torch.cuda.synchronize()
+    fwd, mis, grd = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3]), ev[4].elapsed_time(ev[5])
+    fwd, grd = max_over_ranks(fwd, world), max_over_ranks(grd, world)
+    # inflow recovery: 20 gradient evaluations, steps along -g / max|g| with a backtracking length
+    p0 = np.concatenate([a.speed_guess, [a.theta_guess]])
+    p, Jp, step = p0.copy(), float(J), 0.02
+    for _ in range(20):
+        Jc, gc, _ = prob.misfit_grad(p[:-1], p[-1])
+        Jc, gc = float(Jc), gc.cpu().numpy()
+        while step > 1e-6:
+            q = p - step * gc / np.abs(gc).max()
+            Jq, _ = prob.misfit(q[:-1], q[-1])
+            if float(Jq) < Jc:
+                p, Jp = q, float(Jq)
+                step *= 1.5
+                break
+            step *= 0.5
+    recovery = {"iterations": 20, "J0": float(J), "J": Jp,
+                "speed_err0": float(np.abs(p0[:-1] - a.speed_true).max()),
+                "speed_err": float(np.abs(p[:-1] - a.speed_true).max()),
+                "theta_err0": float(p0[-1] - a.theta_true), "theta_err": float(p[-1] - a.theta_true)}
+    nz, ny, nx = c.shape
+    out = {"workload": f"assim128: {nx}x{ny}x{nz} synthetic city (seed 4), {a.L} level speeds + direction, "
+                       f"{len(a.cols)} lidar columns x {len(a.heights)} heights, mean of the last {a.n_avg} "
+                       f"of {a.nsteps} steps, checkpoints every {a.checkpoint_every}",
+           "forward_ms": fwd, "misfit_ms": mis, "gradient_ms": grd, "ratio": grd / fwd,
+           "J": float(J), "grad_norm": float(torch.linalg.vector_norm(g)), "recovery": recovery}
+    del prob, dom
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(case, seconds: float):
     """The FP64 oracle as it stands, on all host cores, over whole-lattice steps of this workload."""
     import numpy as np
@@ -319,6 +383,9 @@ def run_ours(args, rank, world):
 
     variants = {}
     for st in [v for v in args.variants.split(",") if v and v != args.store]:
+        if st == "adjoint":
+            variants[st] = adjoint_leg(world)
+            continue
         if st in ("stg", "stg_s10"):
             # FP32 with the synthetic von Karman inflow (App. F) on the inflow faces: 64 modes,
             # evaluated every step, or every 10 steps with linear interpolation in between

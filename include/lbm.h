@@ -256,6 +256,63 @@ lbm_status lbm_stg_disable(lbm_domain *d);
  * turbulent faces (bit k = face k).  Any output may be NULL.  LBM_EINVAL when not configured. */
 lbm_status lbm_stg_reference(const lbm_domain *d, double *u_ref, double *e_c, int *faces);
 
+/* ---------------------------------------------------------------------------------------------
+ * Boundary assimilation: virtual-lidar misfit and its discrete-adjoint gradient with respect to
+ * the inflow parameters.  (The paper fits the inflow to Doppler-lidar profiles by Kriging, Sec. 3
+ * and App. A; these calls give the gradient of the same fit, so the inflow can be recovered by
+ * gradient descent.)
+ *
+ * Forward model (FP32 storage, no body force, no rotation, synthetic inflow off):
+ *   1. lbm_set_inflow_profile(speed, L, theta) and lbm_init_fields(NULL, NULL): every non-solid
+ *      cell starts at f^eq of the profile velocity u_b(z) (rho = 1, equilibrium cells rho_b);
+ *   2. n_steps fused steps (lbm_step); the domain is left at step n_steps;
+ *   3. the lidar samples (u, v, w, rho) at cells (ij[c], k[h]) after each of the last n_avg
+ *      states (the states n_steps - n_avg + 1 .. n_steps; state 0 is the initial state) and
+ *      averages them in FP64: mean[c][h][4];
+ *   4. J = sum over c, h of (mean_u - target_u)^2 + (mean_v - target_v)^2.
+ * Gradient (lbm_lidar_misfit_grad): the exact derivative of the discrete forward model (up to
+ * FP32 rounding) with respect to speed[0..L-1] and theta, by the discrete adjoint of every step
+ * (streaming with every face rule, the LES collision D.1-D.11, equilibrium boundary cells, the
+ * initial state), run backwards in segments of checkpoint_every steps that are recomputed from
+ * checkpoints, with FP64 accumulation of the parameter gradient.  At a cell with Q = 0 the
+ * derivative of the Smagorinsky term is taken as 0.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct {
+    int n_steps;            /* T >= 1 */
+    int n_avg;              /* 1 <= n_avg <= T + 1: the last n_avg states are averaged */
+    int checkpoint_every;   /* K >= 1: gradient only; a checkpoint every K states, segments of
+                               K steps recomputed in the reverse sweep */
+} lbm_adjoint_params;
+
+/* Device workspace bytes for ncol x nh samples; gradient != 0: for lbm_lidar_misfit_grad, which
+ * holds ceil(T/K) checkpoints, min(K, T) segment states and two adjoint lattices of 19 N floats
+ * each (plus O(N) bytes); gradient == 0: for lbm_lidar_misfit (O(N) bytes).  0 on bad arguments. */
+size_t lbm_adjoint_workspace_bytes(const lbm_domain *d, const lbm_adjoint_params *p, int ncol, int nh,
+                                   int gradient);
+
+/* Run the forward model and evaluate the misfit.
+ *   speed, L, theta  inflow parameters (HOST), as lbm_set_inflow_profile
+ *   ij, k            HOST int[ncol][2] column positions (x, y) and int[nh] cell heights; every
+ *                    sampled cell must be a fluid cell (LBM_EINVAL otherwise, checked on the GPU)
+ *   target           DEVICE float[ncol][nh][2] target mean (u, v), or NULL (no misfit)
+ *   workspace        DEVICE, 256-byte aligned, ws_bytes >= lbm_adjoint_workspace_bytes(.., 0)
+ *   out              DEVICE double[1]: J (not written when target is NULL); may be NULL
+ *   mean             DEVICE double[ncol][nh][4] mean (u, v, w, rho), or NULL
+ * Synchronises the stream once (sample check) before the steps; the rest is asynchronous. */
+lbm_status lbm_lidar_misfit(lbm_domain *d, const lbm_adjoint_params *p, const float *speed, int L,
+                            float theta, const int *ij, int ncol, const int *k, int nh,
+                            const float *target, void *workspace, size_t ws_bytes, double *out,
+                            double *mean);
+
+/* The same forward run, then the reverse sweep.
+ *   workspace  ws_bytes >= lbm_adjoint_workspace_bytes(.., 1)
+ *   out        DEVICE double[L + 2]: out[0] = J, out[1 + l] = dJ/dspeed[l], out[1 + L] = dJ/dtheta
+ * Asynchronous after the sample check; the domain is left at step n_steps of the forward run. */
+lbm_status lbm_lidar_misfit_grad(lbm_domain *d, const lbm_adjoint_params *p, const float *speed,
+                                 int L, float theta, const int *ij, int ncol, const int *k, int nh,
+                                 const float *target, void *workspace, size_t ws_bytes, double *out,
+                                 double *mean);
+
 /* Message of the last failed call on this domain ("" if none).  Never NULL. */
 const char *lbm_last_error(const lbm_domain *d);
 

@@ -194,6 +194,19 @@ bool has_force(const lbm_domain *d) {
 }  // namespace
 
 namespace lbm {
+void profile_level_weights(int L, int nz, int k, int &l0, int &l1, double &w1) {
+    if (nz % L == 0) {   // equal-height blocks
+        l0 = l1 = k / (nz / L);
+        w1 = 0.0;
+        return;
+    }
+    const double pos = (k + 0.5) * L / nz - 0.5;   // in units of level centres
+    if (pos <= 0.0) { l0 = l1 = 0; w1 = 0.0; return; }
+    if (pos >= L - 1) { l0 = l1 = L - 1; w1 = 0.0; return; }
+    l0 = (int)pos;
+    l1 = l0 + 1;
+    w1 = pos - l0;
+}
 DomainView domain_view(const lbm_domain *d) {
     return DomainView{args_of(d), d->p.store, (d->t & 1) != 0, d->stream};
 }
@@ -321,19 +334,10 @@ lbm_status lbm_set_inflow_profile(lbm_domain *d, const float *speed, int L, floa
     const int nz = d->nz;
     const double c = std::cos((double)theta), s = std::sin((double)theta);
     for (int k = 0; k < nz; ++k) {
-        double v;
-        if (nz % L == 0) {
-            v = speed[k / (nz / L)];
-        } else {
-            const double pos = (k + 0.5) * L / nz - 0.5;   // in units of level centres
-            if (pos <= 0.0) v = speed[0];
-            else if (pos >= L - 1) v = speed[L - 1];
-            else {
-                const int l = (int)pos;
-                const double w = pos - l;
-                v = (1.0 - w) * speed[l] + w * speed[l + 1];
-            }
-        }
+        int l0, l1;
+        double w1;
+        profile_level_weights(L, nz, k, l0, l1, w1);
+        const double v = (1.0 - w1) * (double)speed[l0] + w1 * (double)speed[l1];
         d->ub_host[3 * k] = (float)(v * c);
         d->ub_host[3 * k + 1] = (float)(v * s);
         d->ub_host[3 * k + 2] = 0.0f;

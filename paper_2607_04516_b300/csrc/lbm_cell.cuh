@@ -14,6 +14,20 @@ namespace lbm {
 
 constexpr bool kPairs16 = LBM_PAIRS16 != 0;
 
+// Scale (log2) at which the 16-bit kernels hold populations in registers: the storage scale
+// itself when the collision folds it in (unforced pair form), else 1 (plain g).
+template <int S, bool FORCE> __host__ __device__ constexpr int reg_log2() {
+    return (!FORCE && kPairs16) ? Codec<S>::kLog2 : 0;
+}
+// Shifted equilibrium of an equilibrium cell at register scale 2^L.
+template <int L> LBM_HD void eq_cell_g_s(const StepArgs &a, long long n, float (&g)[Q]) {
+    eq_cell_g(a, n, g);
+    if (L != 0) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] *= (float)(1 << L);
+    }
+}
+
 // ---------------------------------------------------------------- flags from the solid mask
 // Cell kind bits and, for cells that use the store-side bounce-back convention (F_REDIR: interior
 // cells, and cells of a no-slip / free-slip z layer with interior x and y, that have a solid
@@ -353,28 +367,30 @@ template <int S, bool FORCE>
 LBM_HD void store_local_one(const StepArgs &a, int n, uint8_t fl, const float (&g)[Q]) {
     using Cd = Codec<S>;
     using T = typename Cd::T;
+    constexpr int LS = reg_log2<S, FORCE>();
     T *const *P = (T *const *)a.plane;
     if (fl & F_REDIR) {
         const unsigned nb = a.info[n] >> 8;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const bool bb = (nb >> i) & 1u;
-            (bb ? P[i] : P[opp(i)])[bb ? n + a.off[i] : n] = Cd::enc(g[i]);
+            (bb ? P[i] : P[opp(i)])[bb ? n + a.off[i] : n] = Cd::template enc_s<LS>(g[i]);
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) P[opp(i)][n] = Cd::enc(g[i]);
+        for (int i = 0; i < Q; ++i) P[opp(i)][n] = Cd::template enc_s<LS>(g[i]);
     }
     if (fl & F_ZG) {
         int x, y, z;
         cell_coords(a.g, n, x, y, z);
-        store_side<T>(a.g, a.side, x, y, z, g, [](float v) { return Cd::enc(v); });
+        store_side<T>(a.g, a.side, x, y, z, g, [](float v) { return Cd::template enc_s<LS>(v); });
     }
 }
 
 template <int S, bool FORCE>
 LBM_HD void cell2_local(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
     using Cd = Codec<S>;
+    constexpr int LS = reg_log2<S, FORCE>();
     const unsigned short *const *P = (const unsigned short *const *)a.plane;
     uint32_t pk[Q];   // loaded before the flags are known (n1 may be past N: guard region)
 #pragma unroll
@@ -387,11 +403,11 @@ LBM_HD void cell2_local(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
         const int n = c ? n1 : n0;
         float g[Q];
         if (fl & F_EQ) {
-            eq_cell_g(a, n, g);
+            eq_cell_g_s<LS>(a, n, g);
         } else {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) g[i] = Cd::dec_bits(c ? pk[i] >> 16 : pk[i] & 0xffffu);
-            collide<FORCE, kPairs16>(g, a);
+            for (int i = 0; i < Q; ++i) g[i] = Cd::template dec_bits_s<LS>(c ? pk[i] >> 16 : pk[i] & 0xffffu);
+            collide<FORCE, kPairs16, LS>(g, a);
         }
         store_local_one<S, FORCE>(a, n, fl, g);
     }
@@ -400,6 +416,7 @@ LBM_HD void cell2_local(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
 template <int S, bool FORCE>
 LBM_HD void cell2_neighbor_interior(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
     using Cd = Codec<S>;
+    constexpr int LS = reg_log2<S, FORCE>();
     unsigned short *const *P = (unsigned short *const *)a.plane;
     uint32_t pk[Q];   // loaded before the flags are known (guard region after the planes)
 #pragma unroll
@@ -416,18 +433,18 @@ LBM_HD void cell2_neighbor_interior(const StepArgs &a, int n0, int n1, bool v0, 
         const uint8_t fl = c ? f1 : f0;
         float g[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = Cd::dec_bits(c ? pk[i] >> 16 : pk[i] & 0xffffu);
-        collide<FORCE, kPairs16>(g, a);
+        for (int i = 0; i < Q; ++i) g[i] = Cd::template dec_bits_s<LS>(c ? pk[i] >> 16 : pk[i] & 0xffffu);
+        collide<FORCE, kPairs16, LS>(g, a);
         const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
         if (nb) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const bool bb = (nb >> i) & 1u;
-                (bb ? P[opp(i)] : P[i])[bb ? n : n + a.off[i]] = Cd::enc_bits(g[i]);
+                (bb ? P[opp(i)] : P[i])[bb ? n : n + a.off[i]] = Cd::template enc_bits_s<LS>(g[i]);
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) P[i][n + a.off[i]] = Cd::enc_bits(g[i]);
+            for (int i = 0; i < Q; ++i) P[i][n + a.off[i]] = Cd::template enc_bits_s<LS>(g[i]);
         }
     }
 }
@@ -442,6 +459,7 @@ template <int S, bool FORCE>
 LBM_HD void cellp_local(const StepArgs &a, int n0) {
     using Cd = Codec<S>;
     using T = typename Cd::T;
+    constexpr int LS = reg_log2<S, FORCE>();
     const int m = n0 >> 1;
     uint32_t pk[Q];   // inputs; each half is replaced by its cell's encoded result once computed
 #pragma unroll
@@ -455,20 +473,20 @@ LBM_HD void cellp_local(const StepArgs &a, int n0) {
         if (fl & F_SOLID) continue;
         float g[Q];
         if (fl & F_EQ) {
-            eq_cell_g(a, n0 + c, g);
+            eq_cell_g_s<LS>(a, n0 + c, g);
         } else {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) g[i] = Cd::dec_bits(c ? pk[i] >> 16 : pk[i] & 0xffffu);
-            collide<FORCE, kPairs16>(g, a);
+            for (int i = 0; i < Q; ++i) g[i] = Cd::template dec_bits_s<LS>(c ? pk[i] >> 16 : pk[i] & 0xffffu);
+            collide<FORCE, kPairs16, LS>(g, a);
         }
         if (fl & F_ZG) {
             int x, y, z;
             cell_coords(a.g, n0 + c, x, y, z);
-            store_side<T>(a.g, a.side, x, y, z, g, [](float v) { return Cd::enc(v); });
+            store_side<T>(a.g, a.side, x, y, z, g, [](float v) { return Cd::template enc_s<LS>(v); });
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const uint32_t bits = Cd::enc_bits(g[i]);
+            const uint32_t bits = Cd::template enc_bits_s<LS>(g[i]);
             pk[i] = c ? ((pk[i] & 0xffffu) | (bits << 16)) : ((pk[i] & 0xffff0000u) | bits);
         }
     }
@@ -497,6 +515,7 @@ LBM_HD void cellp_local(const StepArgs &a, int n0) {
 template <int S, bool FORCE>
 LBM_HD void cellp_neighbor_interior(const StepArgs &a, int n0) {
     using Cd = Codec<S>;
+    constexpr int LS = reg_log2<S, FORCE>();
     unsigned short *const *P = (unsigned short *const *)a.plane;
     const int n1 = n0 + 1;
     uint32_t pk[Q];   // loaded before the flags are known (guard region after the planes)
@@ -515,11 +534,11 @@ LBM_HD void cellp_neighbor_interior(const StepArgs &a, int n0) {
         if (!(c ? l1 : l0)) continue;
         float g[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = Cd::dec_bits(c ? pk[i] >> 16 : pk[i] & 0xffffu);
-        collide<FORCE, kPairs16>(g, a);
+        for (int i = 0; i < Q; ++i) g[i] = Cd::template dec_bits_s<LS>(c ? pk[i] >> 16 : pk[i] & 0xffffu);
+        collide<FORCE, kPairs16, LS>(g, a);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const uint32_t bits = Cd::enc_bits(g[i]);
+            const uint32_t bits = Cd::template enc_bits_s<LS>(g[i]);
             pk[i] = c ? ((pk[i] & 0xffffu) | (bits << 16)) : ((pk[i] & 0xffff0000u) | bits);
         }
     }
@@ -541,6 +560,130 @@ LBM_HD void cellp_neighbor_interior(const StepArgs &a, int n0) {
             (bb ? P[opp(i)] : P[i])[bb ? n : n + a.off[i]] = (unsigned short)(c ? pk[i] >> 16 : pk[i] & 0xffffu);
         }
     }
+}
+
+// ---------------------------------------------------------------- both cells in one collision
+// Unforced 16-bit steps: the two cells of a thread go through collide2 together (FP32x2
+// instructions), decoded from and encoded to one 32-bit word per direction.  A lane whose cell is
+// solid computes on whatever the slots hold and is discarded; an equilibrium cell's lane is
+// overwritten with its equilibrium before encoding.
+
+// Overwrite the lanes of equilibrium cells with their equilibrium (register scale 2^L).
+template <int L>
+LBM_HD void eq_lanes(const StepArgs &a, long long n0, long long n1, uint8_t f0, uint8_t f1, float2 (&g)[Q]) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!((c ? f1 : f0) & F_EQ)) continue;
+        float ge[Q];
+        eq_cell_g_s<L>(a, c ? n1 : n0, ge);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) (c ? g[i].y : g[i].x) = ge[i];
+    }
+}
+
+// pk: the pair's 19 words (input), f0 / f1: its flags
+template <int S>
+LBM_HD void cellp_local_dual_body(const StepArgs &a, int n0, uint32_t (&pk)[Q], uint8_t f0, uint8_t f1) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    constexpr int LS = Cd::kLog2;
+    const int m = n0 >> 1;
+    if ((f0 & f1) & F_SOLID) return;
+    float2 g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = Cd::template dec2<LS>(pk[i]);
+    collide2<LS>(g, a);
+    if ((f0 | f1) & F_EQ) eq_lanes<LS>(a, n0, n0 + 1, f0, f1, g);
+    if ((f0 | f1) & F_ZG) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const uint8_t fl = c ? f1 : f0;
+            if (!(fl & F_ZG) || (fl & F_SOLID)) continue;
+            float gc[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) gc[i] = c ? g[i].y : g[i].x;
+            int x, y, z;
+            cell_coords(a.g, n0 + c, x, y, z);
+            store_side<T>(a.g, a.side, x, y, z, gc, [](float v) { return Cd::template enc_s<LS>(v); });
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) pk[i] = Cd::template enc2<LS>(g[i]);
+    // one 4-byte store per plane, unless a cell of the pair is solid (its slots may be receiving a
+    // neighbour's bounce-back store) or redirects links
+    if (!((f0 | f1) & (F_SOLID | F_REDIR))) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) ((uint32_t *)a.plane[opp(i)])[m] = pk[i];
+        return;
+    }
+    unsigned short *const *P = (unsigned short *const *)a.plane;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const uint8_t fl = c ? f1 : f0;
+        if (fl & F_SOLID) continue;
+        const int n = n0 + c;
+        const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const bool bb = (nb >> i) & 1u;
+            (bb ? P[i] : P[opp(i)])[bb ? n + a.off[i] : n] = (unsigned short)(c ? pk[i] >> 16 : pk[i] & 0xffffu);
+        }
+    }
+}
+
+// pk: the gathered pair (low half: cell n0), f0 / f1: flags (F_SOLID for a cell that does not exist)
+template <int S>
+LBM_HD void cell2_neighbor_interior_dual_body(const StepArgs &a, int n0, int n1, uint32_t (&pk)[Q], uint8_t f0,
+                                              uint8_t f1) {
+    using Cd = Codec<S>;
+    constexpr int LS = Cd::kLog2;
+    unsigned short *const *P = (unsigned short *const *)a.plane;
+    const bool l0 = !(f0 & (F_SOLID | F_FACE)), l1 = !(f1 & (F_SOLID | F_FACE));
+    if (!l0 && !l1) return;
+    float2 g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = Cd::template dec2<LS>(pk[i]);
+    collide2<LS>(g, a);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) pk[i] = Cd::template enc2<LS>(g[i]);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!(c ? l1 : l0)) continue;
+        const int n = c ? n1 : n0;
+        const uint8_t fl = c ? f1 : f0;
+        const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
+        if (nb) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const bool bb = (nb >> i) & 1u;
+                (bb ? P[opp(i)] : P[i])[bb ? n : n + a.off[i]] = (unsigned short)(c ? pk[i] >> 16 : pk[i] & 0xffffu);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) P[i][n + a.off[i]] = (unsigned short)(c ? pk[i] >> 16 : pk[i] & 0xffffu);
+        }
+    }
+}
+
+template <int S>
+LBM_HD void cellp_local_dual(const StepArgs &a, int n0) {
+    const int m = n0 >> 1;
+    uint32_t pk[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) pk[i] = ld_early_u32((const uint32_t *)a.plane[i] + m);   // before the flags
+    cellp_local_dual_body<S>(a, n0, pk, a.flags[n0], a.flags[n0 + 1]);
+}
+
+template <int S>
+LBM_HD void cell2_neighbor_interior_dual(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
+    const unsigned short *const *P = (const unsigned short *const *)a.plane;
+    uint32_t pk[Q];   // loaded before the flags are known (guard region after the planes)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const unsigned short *p = P[opp(i)] - a.off[i];
+        pk[i] = ld_early_u16(p + n0) | (ld_early_u16(p + n1) << 16);
+    }
+    cell2_neighbor_interior_dual_body<S>(a, n0, n1, pk, v0 ? a.flags[n0] : F_SOLID, v1 ? a.flags[n1] : F_SOLID);
 }
 
 // ---------------------------------------------------------------- post-collision readback

@@ -97,8 +97,11 @@ enum : uint8_t {
 
 // ---------------------------------------------------------------- storage codecs
 template <int S> struct Codec;
+// kLog2: stored value = g * 2^kLog2.  dec_bits_s<L> / enc_bits_s<L> / enc_s<L> work on values
+// scaled by 2^L (L = kLog2: the scale is folded into the collision, L = 0: plain g).
 template <> struct Codec<LBM_F32> {
     using T = float;
+    static constexpr int kLog2 = 0;
     static LBM_HD float dec(T v) { return v; }
     static LBM_HD T enc(float g) { return g; }
 };
@@ -107,15 +110,45 @@ template <> struct Codec<LBM_F16S> {
     static constexpr float kScale = 16384.0f;          // 2^14: keeps |g| ~ 1e-9 .. 4 normal
     static LBM_HD float dec(T v) { return __half2float(v) * (1.0f / kScale); }
     static LBM_HD T enc(float g) { return __float2half_rn(g * kScale); }
+    static constexpr int kLog2 = 14;
     static LBM_HD float dec_bits(unsigned b) { return dec(__ushort_as_half((unsigned short)b)); }
     static LBM_HD unsigned short enc_bits(float g) { return __half_as_ushort(enc(g)); }
+    template <int L> static LBM_HD float dec_bits_s(unsigned b) {
+        const float v = __half2float(__ushort_as_half((unsigned short)b));
+        return L == kLog2 ? v : v * (1.0f / kScale);
+    }
+    template <int L> static LBM_HD T enc_s(float g) { return __float2half_rn(L == kLog2 ? g : g * kScale); }
+    template <int L> static LBM_HD unsigned short enc_bits_s(float g) { return __half_as_ushort(enc_s<L>(g)); }
+    // two cells in one 32-bit word (low half: first cell)
+    template <int L> static LBM_HD float2 dec2(uint32_t u) {
+        const float2 v = __half22float2(__halves2half2(__ushort_as_half((unsigned short)(u & 0xffffu)),
+                                                       __ushort_as_half((unsigned short)(u >> 16))));
+        return L == kLog2 ? v : make_float2(v.x * (1.0f / kScale), v.y * (1.0f / kScale));
+    }
+    template <int L> static LBM_HD uint32_t enc2(float2 g) {
+        const __half2 h = __float22half2_rn(L == kLog2 ? g : make_float2(g.x * kScale, g.y * kScale));
+        return (uint32_t)__half_as_ushort(__low2half(h)) | ((uint32_t)__half_as_ushort(__high2half(h)) << 16);
+    }
 };
 template <> struct Codec<LBM_BF16S> {
     using T = __nv_bfloat16;
     static LBM_HD float dec(T v) { return __bfloat162float(v); }
     static LBM_HD T enc(float g) { return __float2bfloat16_rn(g); }
+    static constexpr int kLog2 = 0;
     static LBM_HD float dec_bits(unsigned b) { return dec(__ushort_as_bfloat16((unsigned short)b)); }
     static LBM_HD unsigned short enc_bits(float g) { return __bfloat16_as_ushort(enc(g)); }
+    template <int L> static LBM_HD float dec_bits_s(unsigned b) { return dec_bits(b); }
+    template <int L> static LBM_HD T enc_s(float g) { return enc(g); }
+    template <int L> static LBM_HD unsigned short enc_bits_s(float g) { return enc_bits(g); }
+    template <int L> static LBM_HD float2 dec2(uint32_t u) {
+        return __bfloat1622float2(__halves2bfloat162(__ushort_as_bfloat16((unsigned short)(u & 0xffffu)),
+                                                     __ushort_as_bfloat16((unsigned short)(u >> 16))));
+    }
+    template <int L> static LBM_HD uint32_t enc2(float2 g) {
+        const __nv_bfloat162 h = __float22bfloat162_rn(g);
+        return (uint32_t)__bfloat16_as_ushort(__low2bfloat16(h)) |
+               ((uint32_t)__bfloat16_as_ushort(__high2bfloat16(h)) << 16);
+    }
 };
 
 // ---------------------------------------------------------------- early loads
@@ -206,6 +239,26 @@ LBM_HD int zfast_mask(const Geo &G) {
     return (ok(G.face[4]) ? 1 : 0) | (ok(G.face[5]) ? 2 : 0);
 }
 
+// ---------------------------------------------------------------- special functions
+// 1/x and square roots of the one-cell collision through the GPU's special-function unit
+// (__fdividef, rsqrtf: relative error ~1e-7, inside the FP32 rounding the step accumulates anyway;
+// measured faster than the IEEE forms in the FP32 step kernels); host builds take the exact forms.
+LBM_HD float rcp_fast(float x) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(1.0f, x);
+#else
+    return 1.0f / x;
+#endif
+}
+LBM_HD float sqrt_pos_fast(float x) {   // x > 0
+#ifdef __CUDA_ARCH__
+    return x * rsqrtf(x);
+#else
+    return sqrtf(x);
+#endif
+}
+LBM_HD float sqrt_nonneg_fast(float x) { return x > 0.0f ? sqrt_pos_fast(x) : 0.0f; }
+
 // ---------------------------------------------------------------- physics (FP32)
 // Equilibrium in shifted form: g^eq_i = f^eq_i - w_i = w_i (drho + rho (3 c.u + 4.5 (c.u)^2
 // - 1.5 u.u))  (Eq. D.4 with c_s^2 = 1/3).
@@ -229,9 +282,12 @@ LBM_HD void equilibrium_shifted(float drho, float ux, float uy, float uz,
 // even part w (drho + rho (4.5 (c.u)^2 - 1.5 u.u)) and an odd part +-3 w rho c.u, with the
 // per-weight coefficients shared by the members of a pair.  Same arithmetic as D.2 / D.4, about
 // half the operations of evaluating the 19 equilibria one by one.
-template <bool FORCE, bool PAIRS = false>
+// LOG2S (PAIRS only): g holds the populations scaled by 2^LOG2S on input and output (the storage
+// scale of FP16 folded into the moments and the equilibrium coefficients; exact, a power of two).
+template <bool FORCE, bool PAIRS = false, int LOG2S = 0>
 LBM_HD void collide(float (&g)[Q], const StepArgs &a) {
     if (!FORCE && PAIRS) {
+        constexpr float S = (float)(1 << LOG2S), iS = 1.0f / S;
         const float s1 = g[1] + g[2], d1 = g[1] - g[2];        // x
         const float s3 = g[3] + g[4], d3 = g[3] - g[4];        // y
         const float s5 = g[5] + g[6], d5 = g[5] - g[6];        // z
@@ -241,30 +297,29 @@ LBM_HD void collide(float (&g)[Q], const StepArgs &a) {
         const float s13 = g[13] + g[14], d13 = g[13] - g[14];  // +x-y
         const float s15 = g[15] + g[16], d15 = g[15] - g[16];  // +x-z
         const float s17 = g[17] + g[18], d17 = g[17] - g[18];  // +y-z
-        const float drho = g[0] + (s1 + s3 + s5) + ((s7 + s9) + (s11 + s13)) + (s15 + s17);
-        const float jx = d1 + d7 + d9 + d13 + d15;
-        const float jy = d3 + d7 + d11 - d13 + d17;
-        const float jz = d5 + d9 + d11 - d15 - d17;
-        const float sxx = s1 + s7 + s9 + s13 + s15;
-        const float syy = s3 + s7 + s11 + s13 + s17;
-        const float szz = s5 + s9 + s11 + s15 + s17;
-        const float sxy = s7 - s13, sxz = s9 - s15, syz = s11 - s17;
+        const float drho = iS * (g[0] + (s1 + s3 + s5) + ((s7 + s9) + (s11 + s13)) + (s15 + s17));
+        const float jx = iS * (d1 + d7 + d9 + d13 + d15);
+        const float jy = iS * (d3 + d7 + d11 - d13 + d17);
+        const float jz = iS * (d5 + d9 + d11 - d15 - d17);
+        const float sxx = iS * (s1 + s7 + s9 + s13 + s15);
+        const float syy = iS * (s3 + s7 + s11 + s13 + s17);
+        const float szz = iS * (s5 + s9 + s11 + s15 + s17);
+        const float sxy = iS * (s7 - s13), sxz = iS * (s9 - s15), syz = iS * (s11 - s17);
         const float rho = 1.0f + drho;
-        const float irho = 1.0f / rho;
+        const float irho = rcp_fast(rho);
         const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
         const float d3r = drho * (1.0f / 3.0f);
         const float pxx = sxx - d3r - jx * ux, pyy = syy - d3r - jy * uy, pzz = szz - d3r - jz * uz;
         const float pxy = sxy - jx * uy, pxz = sxz - jx * uz, pyz = syz - jy * uz;
         const float pp = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (pxy * pxy + pxz * pxz + pyz * pyz);
-        const float qn = sqrtf(2.0f * pp);
-        const float tau_e = 0.5f * (a.tau + sqrtf(a.tau * a.tau + a.c2x18 * qn * irho));
-        const float om = 1.0f / tau_e;
+        const float qn = sqrt_nonneg_fast(2.0f * pp);
+        const float om = 2.0f * rcp_fast(a.tau + sqrt_pos_fast(a.tau * a.tau + a.c2x18 * qn * irho));
         // per weight class w: even part  w (drho - 1.5 rho u.u) + w 4.5 rho (c.u)^2,
         //                     odd part   w 3 rho (c.u);   g* = g + om (g^eq - g)
         const float e = drho - 1.5f * rho * (ux * ux + uy * uy + uz * uz);
-        const float e0 = (1.0f / 3.0f) * e;
-        const float e1 = (1.0f / 18.0f) * e, q1 = 0.25f * rho, a1 = rho * (1.0f / 6.0f);
-        const float e2 = (1.0f / 36.0f) * e, q2 = 0.125f * rho, a2 = rho * (1.0f / 12.0f);
+        const float e0 = (S / 3.0f) * e;
+        const float e1 = (S / 18.0f) * e, q1 = (0.25f * S) * rho, a1 = rho * (S / 6.0f);
+        const float e2 = (S / 36.0f) * e, q2 = (0.125f * S) * rho, a2 = rho * (S / 12.0f);
         g[0] = fmaf(om, e0 - g[0], g[0]);
 #define LBM_PAIR(I, CU, E, Qc, Ac)                              \
         {                                                        \
@@ -302,7 +357,7 @@ LBM_HD void collide(float (&g)[Q], const StepArgs &a) {
         if (cy(i) * cz(i)) syz += cy(i) * cz(i) * g[i];
     }
     const float rho = 1.0f + drho;
-    const float irho = 1.0f / rho;
+    const float irho = rcp_fast(rho);
     // body force of this cell: uniform part + Coriolis 2 rho Omega x (j / rho) = 2 Omega x j (App. E)
     const float Fx = FORCE ? a.fx + 2.0f * (a.oy * jz - a.oz * jy) : 0.0f;
     const float Fy = FORCE ? a.fy + 2.0f * (a.oz * jx - a.ox * jz) : 0.0f;
@@ -318,9 +373,8 @@ LBM_HD void collide(float (&g)[Q], const StepArgs &a) {
     const float pxx = sxx - d3 - jx * ux, pyy = syy - d3 - jy * uy, pzz = szz - d3 - jz * uz;
     const float pxy = sxy - jx * uy, pxz = sxz - jx * uz, pyz = syz - jy * uz;
     const float pp = pxx * pxx + pyy * pyy + pzz * pzz + 2.0f * (pxy * pxy + pxz * pxz + pyz * pyz);
-    const float qn = sqrtf(2.0f * pp);
-    const float tau_e = 0.5f * (a.tau + sqrtf(a.tau * a.tau + a.c2x18 * qn * irho));
-    const float om = 1.0f / tau_e;
+    const float qn = sqrt_nonneg_fast(2.0f * pp);
+    const float om = 2.0f * rcp_fast(a.tau + sqrt_pos_fast(a.tau * a.tau + a.c2x18 * qn * irho));
     float geq[Q];
     equilibrium_shifted(drho, ux, uy, uz, geq);
 #pragma unroll
@@ -334,6 +388,98 @@ LBM_HD void collide(float (&g)[Q], const StepArgs &a) {
         const float cf = cx(i) * Fx + cy(i) * Fy + cz(i) * Fz;
         g[i] += pre * wgt(i) * (3.0f * (cf - uf) + 9.0f * cu * cf);
     }
+}
+
+// ---------------------------------------------------------------- two cells at once
+// Blackwell executes FP32 arithmetic on pairs of values (FADD2 / FMUL2 / FFMA2: one instruction for
+// both lanes of a float2).  collide2 is the unforced pair form of collide<false, true, LOG2S>
+// applied to two cells at once, lane x = first cell, lane y = second: the same arithmetic per lane
+// (D.1, D.4, D.8-D.11, D.2), equal to the one-cell form up to the order of rounding.
+LBM_HD float2 v2(float a) { return make_float2(a, a); }
+LBM_HD float2 add2(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+    return __fadd2_rn(a, b);
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+LBM_HD float2 mul2(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+    return __fmul2_rn(a, b);
+#else
+    return make_float2(a.x * b.x, a.y * b.y);
+#endif
+}
+LBM_HD float2 fma2(float2 a, float2 b, float2 c) {
+#ifdef __CUDA_ARCH__
+    return __ffma2_rn(a, b, c);
+#else
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
+}
+LBM_HD float2 sub2(float2 a, float2 b) { return fma2(b, v2(-1.0f), a); }   // a - b, exact rounding
+LBM_HD float2 fms2(float2 a, float2 b, float2 c) { return fma2(make_float2(-a.x, -a.y), b, c); }   // c - a b
+
+template <int LOG2S>
+LBM_HD void collide2(float2 (&g)[Q], const StepArgs &a) {
+    constexpr float S = (float)(1 << LOG2S), iS = 1.0f / S;
+    const float2 s1 = add2(g[1], g[2]), d1 = sub2(g[1], g[2]);
+    const float2 s3 = add2(g[3], g[4]), d3 = sub2(g[3], g[4]);
+    const float2 s5 = add2(g[5], g[6]), d5 = sub2(g[5], g[6]);
+    const float2 s7 = add2(g[7], g[8]), d7 = sub2(g[7], g[8]);
+    const float2 s9 = add2(g[9], g[10]), d9 = sub2(g[9], g[10]);
+    const float2 s11 = add2(g[11], g[12]), d11 = sub2(g[11], g[12]);
+    const float2 s13 = add2(g[13], g[14]), d13 = sub2(g[13], g[14]);
+    const float2 s15 = add2(g[15], g[16]), d15 = sub2(g[15], g[16]);
+    const float2 s17 = add2(g[17], g[18]), d17 = sub2(g[17], g[18]);
+    const float2 is = v2(iS);
+    const float2 drho = mul2(is, add2(add2(add2(g[0], add2(add2(s1, s3), s5)), add2(add2(s7, s9), add2(s11, s13))),
+                                      add2(s15, s17)));
+    const float2 jx = mul2(is, add2(add2(add2(add2(d1, d7), d9), d13), d15));
+    const float2 jy = mul2(is, add2(sub2(add2(add2(d3, d7), d11), d13), d17));
+    const float2 jz = mul2(is, sub2(sub2(add2(add2(d5, d9), d11), d15), d17));
+    const float2 sxx = mul2(is, add2(add2(add2(add2(s1, s7), s9), s13), s15));
+    const float2 syy = mul2(is, add2(add2(add2(add2(s3, s7), s11), s13), s17));
+    const float2 szz = mul2(is, add2(add2(add2(add2(s5, s9), s11), s15), s17));
+    const float2 sxy = mul2(is, sub2(s7, s13)), sxz = mul2(is, sub2(s9, s15)), syz = mul2(is, sub2(s11, s17));
+    const float2 rho = add2(v2(1.0f), drho);
+    // IEEE division and square roots here (measured faster than the special-function forms when
+    // both lanes go through them together)
+    const float2 irho = make_float2(1.0f / rho.x, 1.0f / rho.y);
+    const float2 ux = mul2(jx, irho), uy = mul2(jy, irho), uz = mul2(jz, irho);
+    const float2 d3r = mul2(drho, v2(1.0f / 3.0f));
+    const float2 pxx = fms2(jx, ux, sub2(sxx, d3r)), pyy = fms2(jy, uy, sub2(syy, d3r)),
+                 pzz = fms2(jz, uz, sub2(szz, d3r));
+    const float2 pxy = fms2(jx, uy, sxy), pxz = fms2(jx, uz, sxz), pyz = fms2(jy, uz, syz);
+    const float2 pd = fma2(pzz, pzz, fma2(pyy, pyy, mul2(pxx, pxx)));
+    const float2 po = fma2(pyz, pyz, fma2(pxz, pxz, mul2(pxy, pxy)));
+    const float2 pp2 = fma2(v2(4.0f), po, mul2(v2(2.0f), pd));   // 2 Pi:Pi
+    const float2 arg = fma2(mul2(v2(a.c2x18), irho), make_float2(sqrtf(pp2.x), sqrtf(pp2.y)), v2(a.tau * a.tau));
+    const float2 om = make_float2(2.0f / (a.tau + sqrtf(arg.x)), 2.0f / (a.tau + sqrtf(arg.y)));
+    const float2 uu = fma2(uz, uz, fma2(uy, uy, mul2(ux, ux)));
+    const float2 e = fms2(mul2(v2(1.5f), rho), uu, drho);
+    const float2 e0 = mul2(v2(S / 3.0f), e);
+    const float2 e1 = mul2(v2(S / 18.0f), e), q1 = mul2(v2(0.25f * S), rho), a1 = mul2(v2(S / 6.0f), rho);
+    const float2 e2 = mul2(v2(S / 36.0f), e), q2 = mul2(v2(0.125f * S), rho), a2 = mul2(v2(S / 12.0f), rho);
+    g[0] = fma2(om, sub2(e0, g[0]), g[0]);
+#define LBM_PAIR2(I, CU, E, Qc, Ac)                                        \
+    {                                                                     \
+        const float2 cu_ = (CU);                                          \
+        const float2 sym_ = fma2(mul2(Qc, cu_), cu_, E);                  \
+        const float2 asym_ = mul2(Ac, cu_);                               \
+        g[I] = fma2(om, sub2(add2(sym_, asym_), g[I]), g[I]);             \
+        g[I + 1] = fma2(om, sub2(sub2(sym_, asym_), g[I + 1]), g[I + 1]); \
+    }
+    LBM_PAIR2(1, ux, e1, q1, a1)
+    LBM_PAIR2(3, uy, e1, q1, a1)
+    LBM_PAIR2(5, uz, e1, q1, a1)
+    LBM_PAIR2(7, add2(ux, uy), e2, q2, a2)
+    LBM_PAIR2(9, add2(ux, uz), e2, q2, a2)
+    LBM_PAIR2(11, add2(uy, uz), e2, q2, a2)
+    LBM_PAIR2(13, sub2(ux, uy), e2, q2, a2)
+    LBM_PAIR2(15, sub2(ux, uz), e2, q2, a2)
+    LBM_PAIR2(17, sub2(uy, uz), e2, q2, a2)
+#undef LBM_PAIR2
 }
 
 // ---------------------------------------------------------------- boundary resolution
@@ -357,44 +503,63 @@ struct Loc {
     long long idx;
 };
 
-LBM_HD Loc gather_loc_B(const Geo &G, const uint8_t *flags, int px, int py, int pz, int i) {
-    int s[3] = {px - cx(i), py - cy(i), pz - cz(i)};
-    const long long self = cell_of(G, px, py, pz);
-    bool bb = false;
+// Source of population i entering fluid cell p: bounce-back (bb), or population d of cell src,
+// with zg the first outflow face the source position was clamped onto (-1: none).
+struct Src {
+    bool bb;
+    int d;
+    int zg;
+    int s[3];
+    long long src;
+};
+
+LBM_HD Src resolve_source(const Geo &G, const uint8_t *flags, int px, int py, int pz, int i) {
+    Src r{false, i, -1, {px - cx(i), py - cy(i), pz - cz(i)}, 0};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (s[a] < 0 && G.face[2 * a] == LBM_FACE_NOSLIP) bb = true;
-        if (s[a] >= dim(G, a) && G.face[2 * a + 1] == LBM_FACE_NOSLIP) bb = true;
+        if (r.s[a] < 0 && G.face[2 * a] == LBM_FACE_NOSLIP) r.bb = true;
+        if (r.s[a] >= dim(G, a) && G.face[2 * a + 1] == LBM_FACE_NOSLIP) r.bb = true;
     }
-    int d = i;
-    int zg = -1;   // first outflow face the source was clamped onto
-    if (!bb) {
+    if (r.bb) return r;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int n = dim(G, a);
-            if (s[a] >= 0 && s[a] < n) continue;
-            const int hi = s[a] >= n;
-            const int k = G.face[2 * a + hi];
-            if (k == LBM_FACE_PERIODIC) {
-                s[a] = hi ? s[a] - n : s[a] + n;
-            } else {
-                s[a] = hi ? n - 1 : 0;
-                if (k == LBM_FACE_FREESLIP) d = mirror(d, a);
-                if (k == LBM_FACE_OUTFLOW_ZG && zg < 0) zg = 2 * a + hi;
-            }
-        }
-        const long long src = cell_of(G, s[0], s[1], s[2]);
-        if (flags[src] & F_SOLID) bb = true;
-        else if (zg >= 0) {
-            long long fcells;
-            const long long fc = face_cell(G, zg >> 1, s[0], s[1], s[2], fcells);
-            return Loc{1 + zg, (long long)d * fcells + fc};
+    for (int a = 0; a < 3; ++a) {
+        const int n = dim(G, a);
+        if (r.s[a] >= 0 && r.s[a] < n) continue;
+        const int hi = r.s[a] >= n;
+        const int k = G.face[2 * a + hi];
+        if (k == LBM_FACE_PERIODIC) {
+            r.s[a] = hi ? r.s[a] - n : r.s[a] + n;
         } else {
-            return Loc{0, (long long)opp_rt(d) * G.N + src};
+            r.s[a] = hi ? n - 1 : 0;
+            if (k == LBM_FACE_FREESLIP) r.d = mirror(r.d, a);
+            if (k == LBM_FACE_OUTFLOW_ZG && r.zg < 0) r.zg = 2 * a + hi;
         }
+    }
+    r.src = cell_of(G, r.s[0], r.s[1], r.s[2]);
+    if (flags[r.src] & F_SOLID) r.bb = true;
+    return r;
+}
+
+LBM_HD Loc gather_loc_B(const Geo &G, const uint8_t *flags, int px, int py, int pz, int i) {
+    const Src r = resolve_source(G, flags, px, py, pz, i);
+    if (!r.bb) {
+        if (r.zg >= 0) {
+            long long fcells;
+            const long long fc = face_cell(G, r.zg >> 1, r.s[0], r.s[1], r.s[2], fcells);
+            return Loc{1 + r.zg, (long long)r.d * fcells + fc};
+        }
+        return Loc{0, (long long)opp_rt(r.d) * G.N + r.src};
     }
     // bounce-back: f*_opp(i)(p) sits in slot i of p in layout B
-    return Loc{0, (long long)i * G.N + self};
+    return Loc{0, (long long)i * G.N + cell_of(G, px, py, pz)};
+}
+
+// Element (d N + cell) of a population-major lattice holding the post-collision state F* in the
+// plain (unstreamed) layout, F*_d(cell) in slot d, that the fluid cell p gathers as population i.
+LBM_HD long long gather_elem_canon(const Geo &G, const uint8_t *flags, int px, int py, int pz, int i) {
+    const Src r = resolve_source(G, flags, px, py, pz, i);
+    if (r.bb) return (long long)opp_rt(i) * G.N + cell_of(G, px, py, pz);
+    return (long long)r.d * G.N + r.src;
 }
 
 // Up to two coordinates on one axis at which a cell consumes population j of cell p (the plain

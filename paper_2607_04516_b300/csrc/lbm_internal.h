@@ -29,6 +29,9 @@ struct DomainView {
     cudaStream_t stream;
 };
 DomainView domain_view(const lbm_domain *d);
+// Level-to-height mapping of the inflow profile: s(z_k) = (1 - w1) speed[l0] + w1 speed[l1]
+// (equal-height blocks when L divides nz, else linear between level centres).
+void profile_level_weights(int L, int nz, int k, int &l0, int &l1, double &w1);
 lbm_status domain_fail(lbm_domain *d, lbm_status st, const char *msg);
 
 }  // namespace lbm

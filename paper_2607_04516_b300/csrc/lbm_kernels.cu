@@ -19,9 +19,16 @@
 #include "lbm_cell.cuh"
 #include "lbm_internal.h"
 
+// 16-bit storage, unforced steps: both cells of a thread in one FP32x2 collision (1), or one
+// after the other (0); chosen by measurement on B300
+#ifndef LBM_DUAL16
+#define LBM_DUAL16 1
+#endif
+
 namespace lbm {
 
 constexpr int kBlock = 256;
+constexpr bool kDual16 = LBM_DUAL16 != 0;
 
 // ---------------------------------------------------------------- grid wrappers
 #define LBM_CELL_INDEX()                                                   \
@@ -55,7 +62,8 @@ __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_LOCAL) k_step_local(Ste
     } else if constexpr (PACK) {
         const int n0 = (int)(blockIdx.x * 2 * kBlock + 2 * threadIdx.x);
         if (n0 >= a.g.N) return;
-        cellp_local<S, FORCE>(a, n0);
+        if constexpr (!FORCE && kDual16) cellp_local_dual<S>(a, n0);
+        else cellp_local<S, FORCE>(a, n0);
     } else {
         const int n0 = (int)(blockIdx.x * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
         if (n0 >= a.g.N) return;
@@ -81,7 +89,8 @@ __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_NEIGHBOR) k_step_neighb
         } else {
             const int n0 = (int)((blockIdx.x - face_blocks) * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
             if (n0 >= a.g.N) return;
-            cell2_neighbor_interior<S, FORCE>(a, n0, n1, true, n1 < a.g.N);
+            if constexpr (!FORCE && kDual16) cell2_neighbor_interior_dual<S>(a, n0, n1, true, n1 < a.g.N);
+            else cell2_neighbor_interior<S, FORCE>(a, n0, n1, true, n1 < a.g.N);
         }
     } else {
         const long long t = (long long)blockIdx.x * kBlock + threadIdx.x;

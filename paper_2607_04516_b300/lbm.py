@@ -41,6 +41,10 @@ class lbm_stg_params(ctypes.Structure):
                 ("inflow_only", ctypes.c_int), ("stride", ctypes.c_int), ("interpolate", ctypes.c_int)]
 
 
+class lbm_adjoint_params(ctypes.Structure):
+    _fields_ = [("n_steps", ctypes.c_int), ("n_avg", ctypes.c_int), ("checkpoint_every", ctypes.c_int)]
+
+
 # exported symbols and their ctypes signatures (the header is the authority)
 _P, _I, _F, _LL, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_longlong, ctypes.c_size_t
 _PP = ctypes.POINTER(lbm_params)
@@ -66,6 +70,11 @@ SIGNATURES = {
     "lbm_stg_configure": (_I, [_P, ctypes.POINTER(lbm_stg_params), _P, _P, _SZ]),
     "lbm_stg_disable": (_I, [_P]),
     "lbm_stg_reference": (_I, [_P, _P, _P, _P]),
+    "lbm_adjoint_workspace_bytes": (_SZ, [_P, ctypes.POINTER(lbm_adjoint_params), _I, _I, _I]),
+    "lbm_lidar_misfit": (_I, [_P, ctypes.POINTER(lbm_adjoint_params), _P, _I, _F, _P, _I, _P, _I, _P,
+                              _P, _SZ, _P, _P]),
+    "lbm_lidar_misfit_grad": (_I, [_P, ctypes.POINTER(lbm_adjoint_params), _P, _I, _F, _P, _I, _P, _I,
+                                   _P, _P, _SZ, _P, _P]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
     "lbm_destroy": (None, [_P]),
 }
@@ -242,6 +251,42 @@ def lbm_stg_reference(dom):
     return u.value, e, f.value
 
 
+def make_adjoint_params(n_steps: int, n_avg: int, checkpoint_every: int = 100) -> lbm_adjoint_params:
+    p = lbm_adjoint_params()
+    p.n_steps, p.n_avg, p.checkpoint_every = int(n_steps), int(n_avg), int(checkpoint_every)
+    return p
+
+
+def lbm_adjoint_workspace_bytes(dom, params: lbm_adjoint_params, ncol: int, nh: int, gradient: bool) -> int:
+    return load(False).lbm_adjoint_workspace_bytes(dom, ctypes.byref(params), int(ncol), int(nh),
+                                                   int(bool(gradient)))
+
+
+def _lidar_args(speed, ij, k):
+    sp = np.ascontiguousarray(speed, np.float32)
+    ij = np.ascontiguousarray(ij, np.int32).reshape(-1, 2)
+    k = np.ascontiguousarray(k, np.int32).reshape(-1)
+    return sp, ij, k
+
+
+def lbm_lidar_misfit(dom, params, speed, theta, ij, k, target, workspace, out=None, mean=None):
+    """Host ``speed``, ``ij`` (ncol, 2), ``k`` (nh,); CUDA ``target`` float32 (ncol, nh, 2) or
+    None, ``workspace`` uint8, ``out`` float64 (1,) and ``mean`` float64 (ncol, nh, 4) or None."""
+    sp, ij, k = _lidar_args(speed, ij, k)
+    _check(load().lbm_lidar_misfit(dom, ctypes.byref(params), sp.ctypes.data, len(sp), float(theta),
+                                   ij.ctypes.data, ij.shape[0], k.ctypes.data, k.shape[0], _ptr(target),
+                                   _ptr(workspace), workspace.numel(), _ptr(out), _ptr(mean)), dom)
+
+
+def lbm_lidar_misfit_grad(dom, params, speed, theta, ij, k, target, workspace, out, mean=None):
+    """As ``lbm_lidar_misfit``; ``out`` CUDA float64 (L + 2,) = J, dJ/dspeed[L], dJ/dtheta."""
+    sp, ij, k = _lidar_args(speed, ij, k)
+    _check(load().lbm_lidar_misfit_grad(dom, ctypes.byref(params), sp.ctypes.data, len(sp), float(theta),
+                                        ij.ctypes.data, ij.shape[0], k.ctypes.data, k.shape[0],
+                                        _ptr(target), _ptr(workspace), workspace.numel(), _ptr(out),
+                                        _ptr(mean)), dom)
+
+
 def lbm_destroy(dom):
     load(False).lbm_destroy(dom)
 
@@ -339,6 +384,83 @@ class Domain:
 
     def stg_reference(self):
         return lbm_stg_reference(self.dom)
+
+
+class LidarProblem:
+    """Virtual-lidar misfit of a domain's inflow (see ``lbm_lidar_misfit_grad`` in ``lbm.h``):
+    columns ``cols`` (ncol, 2) = (x, y), heights ``heights`` (nh,), target mean (u, v)
+    (ncol, nh, 2); workspaces are torch tensors on the domain's device, allocated on first use."""
+
+    def __init__(self, domain: Domain, cols, heights, target, n_steps: int, n_avg: int,
+                 checkpoint_every: int = 100):
+        import torch
+        self.domain = domain
+        self.cols = np.ascontiguousarray(cols, np.int32).reshape(-1, 2)
+        self.heights = np.ascontiguousarray(heights, np.int32).reshape(-1)
+        self.params = make_adjoint_params(n_steps, n_avg, checkpoint_every)
+        self.target = torch.as_tensor(np.asarray(target, np.float32), device=domain.device).contiguous()
+        self._ws = {}
+
+    def _workspace(self, grad: bool):
+        import torch
+        if grad not in self._ws:
+            nb = lbm_adjoint_workspace_bytes(self.domain.dom, self.params, len(self.cols), len(self.heights), grad)
+            if nb == 0:
+                raise LbmError(-1, "invalid adjoint arguments")
+            self._ws[grad] = torch.empty(nb, dtype=torch.uint8, device=self.domain.device)
+        return self._ws[grad]
+
+    def misfit(self, speed, theta, target=True):
+        """(J, mean (ncol, nh, 4)) as CUDA float64 tensors (J is NaN without a target)."""
+        import torch
+        out = torch.full((1,), float("nan"), dtype=torch.float64, device=self.domain.device)
+        mean = torch.empty((len(self.cols), len(self.heights), 4), dtype=torch.float64, device=self.domain.device)
+        lbm_lidar_misfit(self.domain.dom, self.params, speed, theta, self.cols, self.heights,
+                         self.target if target else None, self._workspace(False), out, mean)
+        return out[0], mean
+
+    def misfit_grad(self, speed, theta):
+        """(J, dJ/d(speed..., theta) (L + 1,), mean) as CUDA float64 tensors."""
+        import torch
+        L = len(speed)
+        out = torch.empty((L + 2,), dtype=torch.float64, device=self.domain.device)
+        mean = torch.empty((len(self.cols), len(self.heights), 4), dtype=torch.float64, device=self.domain.device)
+        lbm_lidar_misfit_grad(self.domain.dom, self.params, speed, theta, self.cols, self.heights,
+                              self.target, self._workspace(True), out, mean)
+        return out[0], out[1:], mean
+
+
+def _autograd_function():
+    import torch
+
+    class LidarMisfit(torch.autograd.Function):
+        """J(p) for p = (speed_0 .. speed_{L-1}, theta) (float64 tensor): the forward call runs the
+        forward model and the discrete adjoint together (``lbm_lidar_misfit_grad``); backward
+        returns the stored gradient times the incoming one."""
+
+        @staticmethod
+        def forward(ctx, p, problem):
+            pc = p.detach().to("cpu", torch.float64).numpy()
+            J, grad, _ = problem.misfit_grad(pc[:-1], float(pc[-1]))
+            ctx.save_for_backward(grad.to(p.device, p.dtype))
+            return J.to(p.device, p.dtype)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (grad,) = ctx.saved_tensors
+            return gJ * grad, None
+
+    return LidarMisfit
+
+
+def lidar_misfit(p, problem: LidarProblem):
+    """Differentiable J(p) (torch.autograd): ``p`` = (speed_0 .. speed_{L-1}, theta)."""
+    global _LidarMisfit
+    try:
+        fn = _LidarMisfit
+    except NameError:
+        fn = _LidarMisfit = _autograd_function()
+    return fn.apply(p, problem)
 
 
 def glups(cells: int, steps: int, seconds: float) -> float:
