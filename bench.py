@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10,adjoint",
                     help="extra storage kinds timed after the main measurement ('' = none)")
     ap.add_argument("--e2e-steps", type=int, default=1000)
+    ap.add_argument("--adjoint-steps", type=int, default=2000,
+                    help="steps of the assimilation run in the adjoint leg (2000 = the full workload)")
+    ap.add_argument("--adjoint-recovery", type=int, default=20, help="descent iterations in the adjoint leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -241,7 +244,7 @@ def e2e_glups(dom, case, steps: int, world: int):
             dt * 1e3 / steps)
 
 
-def adjoint_leg(world: int):
+def adjoint_leg(world: int, nsteps: int = 2000, iters: int = 20):
     """Boundary assimilation (128 x 128 x 48 city, 24 level speeds + direction, 8 lidar columns x
     10 heights averaged over the last 500 of 2000 steps, checkpoints every 100 steps): time of the
     misfit gradient (forward run + reverse sweep, lbm_lidar_misfit_grad) against 2000 plain FP32
@@ -250,6 +253,8 @@ def adjoint_leg(world: int):
     import torch
     from paper_2607_04516_b300 import lbm, synth
     a = synth.assimilation_case()
+    if nsteps != a.nsteps:   # shortened run (profiling): same lattice, fewer steps
+        a.nsteps, a.n_avg, a.checkpoint_every = nsteps, max(1, nsteps // 4), max(1, min(100, nsteps // 4))
     c = a.case
     dom = lbm.Domain(c.solid, c.faces, c.tau, c.cs, "f32")
     prob = lbm.LidarProblem(dom, a.cols, a.heights, np.zeros((len(a.cols), len(a.heights), 2), np.float32),
@@ -279,7 +284,7 @@ def adjoint_leg(world: int):
     # inflow recovery: 20 gradient evaluations, steps along -g / max|g| with a backtracking length
     p0 = np.concatenate([a.speed_guess, [a.theta_guess]])
     p, Jp, step = p0.copy(), float(J), 0.02
-    for _ in range(20):
+    for _ in range(iters):
         Jc, gc, _ = prob.misfit_grad(p[:-1], p[-1])
         Jc, gc = float(Jc), gc.cpu().numpy()
         while step > 1e-6:
@@ -290,7 +295,7 @@ def adjoint_leg(world: int):
                 step *= 1.5
                 break
             step *= 0.5
-    recovery = {"iterations": 20, "J0": float(J), "J": Jp,
+    recovery = {"iterations": iters, "J0": float(J), "J": Jp,
                 "speed_err0": float(np.abs(p0[:-1] - a.speed_true).max()),
                 "speed_err": float(np.abs(p[:-1] - a.speed_true).max()),
                 "theta_err0": float(p0[-1] - a.theta_true), "theta_err": float(p[-1] - a.theta_true)}
@@ -384,7 +389,7 @@ def run_ours(args, rank, world):
     variants = {}
     for st in [v for v in args.variants.split(",") if v and v != args.store]:
         if st == "adjoint":
-            variants[st] = adjoint_leg(world)
+            variants[st] = adjoint_leg(world, args.adjoint_steps, args.adjoint_recovery)
             continue
         if st in ("stg", "stg_s10"):
             # FP32 with the synthetic von Karman inflow (App. F) on the inflow faces: 64 modes,
