@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--store", default="f32", choices=list(STORE_BYTES))
     ap.add_argument("--workload", default="city400", choices=list(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10,adjoint",
+    ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10,adjoint,ensemble",
                     help="extra storage kinds timed after the main measurement ('' = none)")
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--adjoint-steps", type=int, default=2000,
@@ -310,6 +310,57 @@ def adjoint_leg(world: int, nsteps: int = 2000, iters: int = 20):
     return out
 
 
+def ensemble_leg(world: int, steps: int = 40):
+    """Batched ensemble: a wind rose of 16 inflow directions x 2 speeds on a 256x256x64 city plus 8
+    domains of uneven size (96x96x32 .. 320x192x64), FP32.  Aggregate GLUPS (all cells of all members
+    per second) of one single-domain launch per member and step, against the batched launch in the
+    autotuned shape, stepped directly and replayed from a CUDA graph; CUDA events on the batch's
+    stream."""
+    import numpy as np
+    import torch
+    from paper_2607_04516_b300 import lbm, synth
+    cases = synth.ensemble_cases() + synth.uneven_cases()
+    cells = int(sum(c.solid.size for c in cases))
+    stream = torch.cuda.Stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1])
+
+    with torch.cuda.stream(stream):
+        doms = []
+        for c in cases:
+            d = lbm.Domain(c.solid, c.faces, c.tau, c.cs, "f32", stream=stream)
+            d.set_inflow_profile(c.speed.astype(np.float32), c.theta)
+            d.init_fields()
+            doms.append(d)
+        b = lbm.Batch(doms, stream=stream)
+        b.shape = 4
+        b.step(2)
+        seq = timed(lambda: b.step(steps))
+        choice, tune_ms = b.autotune(trial_steps=10)
+        bat = timed(lambda: b.step(steps))
+        b.capture(steps)
+        b.launch()
+        gra = timed(b.launch)
+    barrier(world)
+    seq, bat, gra = (max_over_ranks(x, world) for x in (seq, bat, gra))
+    g = lambda ms: cells * steps * world / (ms / 1e3) / 1e9
+    out = {"workload": f"16 directions x 2 speeds on a 256x256x64 city (seed 3) + 8 uneven domains "
+                       f"96x96x32 .. 320x192x64; {len(cases)} members, {cells} cells, FP32",
+           "steps": steps, "sequential_glups": g(seq), "batched_glups": g(bat), "graph_glups": g(gra),
+           "graph_vs_sequential": seq / gra, "shape": lbm.BATCH_SHAPES[choice],
+           "autotune_ms_per_step": dict(zip(lbm.BATCH_SHAPES, tune_ms))}
+    del b, doms
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(case, seconds: float):
     """The FP64 oracle as it stands, on all host cores, over whole-lattice steps of this workload."""
     import numpy as np
@@ -390,6 +441,9 @@ def run_ours(args, rank, world):
     for st in [v for v in args.variants.split(",") if v and v != args.store]:
         if st == "adjoint":
             variants[st] = adjoint_leg(world, args.adjoint_steps, args.adjoint_recovery)
+            continue
+        if st == "ensemble":
+            variants[st] = ensemble_leg(world)
             continue
         if st in ("stg", "stg_s10"):
             # FP32 with the synthetic von Karman inflow (App. F) on the inflow faces: 64 modes,

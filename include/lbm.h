@@ -313,6 +313,61 @@ lbm_status lbm_lidar_misfit_grad(lbm_domain *d, const lbm_adjoint_params *p, con
                                  const float *target, void *workspace, size_t ws_bytes, double *out,
                                  double *mean);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched ensembles: several domains (inflow directions and speeds, lattices of uneven size)
+ * advanced together, one kernel launch per time step for all of them.  (The paper runs one case
+ * at a time, Sec. 3; an ensemble of inflow conditions is what the assimilation and the wind-rose
+ * studies iterate over.)
+ *
+ * Members keep their own workspaces, profiles and state; every member must use the same storage
+ * kind, have no body force, no rotation and no synthetic inflow, and have taken steps of the same
+ * parity (they then advance in lockstep: lbm_steps_done grows by the same amount on each).  A
+ * batched step computes exactly what lbm_step computes on each member.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch; /* opaque */
+
+/* Device workspace bytes for a batch of n members (step arguments and block tables, about 1 KB per
+ * member); 0 if n is outside [1, 4096]. */
+size_t lbm_batch_workspace_bytes(int n);
+
+/* Group n domains.  workspace: DEVICE, 256-byte aligned, ws_bytes >= lbm_batch_workspace_bytes(n),
+ * owned by the caller.  stream: cudaStream_t as void* (NULL = default stream; capture needs a
+ * non-default one).  LBM_EINVAL for mixed storage kinds, forced or turbulent-inflow members or a
+ * member given twice; LBM_ESTATE if the members' step counts differ in parity.  Synchronises the
+ * stream once (table upload). */
+lbm_status lbm_batch_create(lbm_domain *const *domains, int n, void *workspace, size_t ws_bytes,
+                            void *stream, lbm_batch **out);
+
+/* Advance every member by nsteps >= 0 steps (asynchronous on the batch stream). */
+lbm_status lbm_batch_step(lbm_batch *b, int nsteps);
+
+/* Record nsteps (even, >= 2) batched steps into a CUDA graph kept by the batch (replaces the
+ * previous one).  Nothing runs; the members do not advance. */
+lbm_status lbm_batch_capture(lbm_batch *b, int nsteps);
+
+/* Replay the captured graph: every member advances by the captured number of steps.  LBM_ESTATE
+ * when nothing is captured or the members are not at the parity of the capture. */
+lbm_status lbm_batch_launch(lbm_batch *b);
+
+/* Launch shapes: 0 = kernels compiled for 4 resident blocks per SM, members in the given order;
+ * 1 = 3 blocks per SM, given order; 2 = 4 blocks, largest member first; 3 = 3 blocks, largest
+ * first; 4 = one single-domain launch per member and step (no batching).  The autotuner runs
+ * 2 + trial_steps steps of every shape on the members (they advance by 5 (2 + trial_steps)),
+ * times each with CUDA events and keeps the fastest.  trial_steps even, >= 2.  choice (may be
+ * NULL) receives the chosen shape, ms_per_step (may be NULL) five times in ms per step.
+ * Synchronises the stream; drops a captured graph. */
+lbm_status lbm_batch_autotune(lbm_batch *b, int trial_steps, int *choice, float *ms_per_step);
+
+/* Set / read the launch shape (drops a captured graph). */
+lbm_status lbm_batch_set_shape(lbm_batch *b, int shape);
+int lbm_batch_shape(const lbm_batch *b);
+
+/* Message of the last failed call on this batch.  Never NULL. */
+const char *lbm_batch_last_error(const lbm_batch *b);
+
+/* Release the batch (host memory and its graph); the members and the workspace are untouched. */
+void lbm_batch_destroy(lbm_batch *b);
+
 /* Message of the last failed call on this domain ("" if none).  Never NULL. */
 const char *lbm_last_error(const lbm_domain *d);
 

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liblbm.so")
 SOURCES = [os.path.join(CSRC, "lbm_kernels.cu"), os.path.join(CSRC, "lbm_capi.cu"),
            os.path.join(CSRC, "lbm_noalloc.cu"), os.path.join(CSRC, "lbm_stg.cu"),
-           os.path.join(CSRC, "lbm_adjoint.cu")]
+           os.path.join(CSRC, "lbm_adjoint.cu"), os.path.join(CSRC, "lbm_batch.cu")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

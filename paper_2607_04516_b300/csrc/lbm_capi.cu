@@ -211,6 +211,8 @@ DomainView domain_view(const lbm_domain *d) {
     return DomainView{args_of(d), d->p.store, (d->t & 1) != 0, d->stream};
 }
 lbm_status domain_fail(lbm_domain *d, lbm_status st, const char *msg) { return fail(d, st, "%s", msg); }
+void domain_advance(lbm_domain *d, long long n) { d->t += n; }
+bool domain_stg_on(const lbm_domain *d) { return d->stg.on; }
 }  // namespace lbm
 
 extern "C" {

@@ -772,4 +772,85 @@ LBM_HD void cell_export(const StepArgs &a, long long n, bool layoutA, float *__r
     for (int i = 0; i < Q; ++i) out[(long long)i * a.g.N + n] = g[i];
 }
 
+// ---------------------------------------------------------------- one block of a step kernel
+// The work of block `bid` of a local or neighbour step launch over the lattice of `a` (256-thread
+// blocks); shared by the single-domain kernels and the batched kernel, which places the blocks of
+// several lattices in one grid.
+constexpr int kBlock = 256;
+
+// 16-bit storage, unforced steps: both cells of a thread in one FP32x2 collision (1), or one
+// after the other (0); chosen by measurement on B300
+#ifndef LBM_DUAL16
+#define LBM_DUAL16 1
+#endif
+constexpr bool kDual16 = LBM_DUAL16 != 0;
+
+// cells per thread of the lattice blocks: one for FP32 storage, two for 16-bit storage
+template <int S> __host__ __device__ constexpr int cells_per_thread() { return S == LBM_F32 ? 1 : 2; }
+
+// lattice blocks of a launch over N cells
+template <int S> __host__ __device__ inline unsigned lattice_blocks(long long N) {
+    const long long cpt = cells_per_thread<S>();
+    return (unsigned)(((N + cpt - 1) / cpt + kBlock - 1) / kBlock);
+}
+__host__ __device__ inline unsigned face_blocks_of(long long nface) { return (unsigned)((nface + kBlock - 1) / kBlock); }
+
+template <int S, bool FORCE, bool PACK>
+__device__ __forceinline__ void local_block(const StepArgs &a, unsigned bid) {
+    if constexpr (cells_per_thread<S>() == 1) {
+        const int n = (int)(bid * kBlock + threadIdx.x);
+        if (n >= a.g.N) return;
+        cell_local<S, FORCE>(a, n);
+    } else if constexpr (PACK) {
+        const int n0 = (int)(bid * 2 * kBlock + 2 * threadIdx.x);
+        if (n0 >= a.g.N) return;
+        if constexpr (!FORCE && kDual16) cellp_local_dual<S>(a, n0);
+        else cellp_local<S, FORCE>(a, n0);
+    } else {
+        const int n0 = (int)(bid * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
+        if (n0 >= a.g.N) return;
+        cell2_local<S, FORCE>(a, n0, n1, true, n1 < a.g.N);
+    }
+}
+
+template <int S, bool FORCE, bool PACK>
+__device__ __forceinline__ void neighbor_block(const StepArgs &a, unsigned bid, unsigned face_blocks) {
+    if (bid >= face_blocks) {
+        if constexpr (cells_per_thread<S>() == 1) {
+            const int n = (int)((bid - face_blocks) * kBlock + threadIdx.x);
+            if (n >= a.g.N) return;
+            cell_neighbor_interior<S, FORCE>(a, n);
+        } else if constexpr (PACK) {
+            const int n0 = (int)((bid - face_blocks) * 2 * kBlock + 2 * threadIdx.x);
+            if (n0 >= a.g.N) return;
+            cellp_neighbor_interior<S, FORCE>(a, n0);
+        } else {
+            const int n0 = (int)((bid - face_blocks) * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
+            if (n0 >= a.g.N) return;
+            if constexpr (!FORCE && kDual16) cell2_neighbor_interior_dual<S>(a, n0, n1, true, n1 < a.g.N);
+            else cell2_neighbor_interior<S, FORCE>(a, n0, n1, true, n1 < a.g.N);
+        }
+    } else {
+        const long long t = (long long)bid * kBlock + threadIdx.x;
+        if (t >= a.nface) return;
+        int x, y, z;
+        if (a.ftab) {   // tables cover every face cell
+            if (cell_neighbor_table<S, FORCE>(a, (int)t)) return;
+            const int n = (int)(a.ftab[t] & kFtCell);
+            cell_coords(a.g, n, x, y, z);
+            cell_neighbor_face<S, FORCE>(a, a.flags[n], x, y, z);
+            return;
+        }
+        face_cell_xyz(a.g, t, x, y, z);
+        const int n = (int)cell_of(a.g, x, y, z);
+        const uint8_t fl = a.flags[n];
+        if (fl & F_SOLID) return;
+        if (t >= a.zface_begin && ((a.zfast >> (z == 0 ? 0 : 1)) & 1)) {
+            cell_neighbor_zlayer<S, FORCE>(a, n, fl, z != 0);
+            return;
+        }
+        cell_neighbor_face<S, FORCE>(a, fl, x, y, z);
+    }
+}
+
 }  // namespace lbm

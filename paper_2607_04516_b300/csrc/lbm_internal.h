@@ -33,5 +33,9 @@ DomainView domain_view(const lbm_domain *d);
 // (equal-height blocks when L divides nz, else linear between level centres).
 void profile_level_weights(int L, int nz, int k, int &l0, int &l1, double &w1);
 lbm_status domain_fail(lbm_domain *d, lbm_status st, const char *msg);
+// Step counter bookkeeping for steps launched outside lbm_step (batched launches).
+void domain_advance(lbm_domain *d, long long n);
+// The domain has synthetic inflow turbulence switched on (its steps need the anchor kernel).
+bool domain_stg_on(const lbm_domain *d);
 
 }  // namespace lbm

@@ -19,16 +19,7 @@
 #include "lbm_cell.cuh"
 #include "lbm_internal.h"
 
-// 16-bit storage, unforced steps: both cells of a thread in one FP32x2 collision (1), or one
-// after the other (0); chosen by measurement on B300
-#ifndef LBM_DUAL16
-#define LBM_DUAL16 1
-#endif
-
 namespace lbm {
-
-constexpr int kBlock = 256;
-constexpr bool kDual16 = LBM_DUAL16 != 0;
 
 // ---------------------------------------------------------------- grid wrappers
 #define LBM_CELL_INDEX()                                                   \
@@ -49,26 +40,10 @@ __global__ void k_init(StepArgs a, const float *__restrict__ rho, const float *_
     cell_init<S>(a, n, rho, u);
 }
 
-// cells per thread of the lattice blocks: one for FP32 storage, two for 16-bit storage
-template <int S> __host__ __device__ constexpr int cells_per_thread() { return S == LBM_F32 ? 1 : 2; }
-
 // PACK (16-bit storage with N and nx even): adjacent cell pairs with 4-byte accesses
 template <int S, bool FORCE, bool PACK>
 __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_LOCAL) k_step_local(StepArgs a) {
-    if constexpr (cells_per_thread<S>() == 1) {
-        const int n = (int)(blockIdx.x * kBlock + threadIdx.x);
-        if (n >= a.g.N) return;
-        cell_local<S, FORCE>(a, n);
-    } else if constexpr (PACK) {
-        const int n0 = (int)(blockIdx.x * 2 * kBlock + 2 * threadIdx.x);
-        if (n0 >= a.g.N) return;
-        if constexpr (!FORCE && kDual16) cellp_local_dual<S>(a, n0);
-        else cellp_local<S, FORCE>(a, n0);
-    } else {
-        const int n0 = (int)(blockIdx.x * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
-        if (n0 >= a.g.N) return;
-        cell2_local<S, FORCE>(a, n0, n1, true, n1 < a.g.N);
-    }
+    local_block<S, FORCE, PACK>(a, blockIdx.x);
 }
 
 // Blocks [0, face_blocks) update the face-layer cells (general boundary resolution, ALU heavy);
@@ -77,42 +52,7 @@ __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_LOCAL) k_step_local(Ste
 // two paths.
 template <int S, bool FORCE, bool PACK>
 __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_NEIGHBOR) k_step_neighbor(StepArgs a, unsigned face_blocks) {
-    if (blockIdx.x >= face_blocks) {
-        if constexpr (cells_per_thread<S>() == 1) {
-            const int n = (int)((blockIdx.x - face_blocks) * kBlock + threadIdx.x);
-            if (n >= a.g.N) return;
-            cell_neighbor_interior<S, FORCE>(a, n);
-        } else if constexpr (PACK) {
-            const int n0 = (int)((blockIdx.x - face_blocks) * 2 * kBlock + 2 * threadIdx.x);
-            if (n0 >= a.g.N) return;
-            cellp_neighbor_interior<S, FORCE>(a, n0);
-        } else {
-            const int n0 = (int)((blockIdx.x - face_blocks) * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
-            if (n0 >= a.g.N) return;
-            if constexpr (!FORCE && kDual16) cell2_neighbor_interior_dual<S>(a, n0, n1, true, n1 < a.g.N);
-            else cell2_neighbor_interior<S, FORCE>(a, n0, n1, true, n1 < a.g.N);
-        }
-    } else {
-        const long long t = (long long)blockIdx.x * kBlock + threadIdx.x;
-        if (t >= a.nface) return;
-        int x, y, z;
-        if (a.ftab) {   // tables cover every face cell
-            if (cell_neighbor_table<S, FORCE>(a, (int)t)) return;
-            const int n = (int)(a.ftab[t] & kFtCell);
-            cell_coords(a.g, n, x, y, z);
-            cell_neighbor_face<S, FORCE>(a, a.flags[n], x, y, z);
-            return;
-        }
-        face_cell_xyz(a.g, t, x, y, z);
-        const int n = (int)cell_of(a.g, x, y, z);
-        const uint8_t fl = a.flags[n];
-        if (fl & F_SOLID) return;
-        if (t >= a.zface_begin && ((a.zfast >> (z == 0 ? 0 : 1)) & 1)) {
-            cell_neighbor_zlayer<S, FORCE>(a, n, fl, z != 0);
-            return;
-        }
-        cell_neighbor_face<S, FORCE>(a, fl, x, y, z);
-    }
+    neighbor_block<S, FORCE, PACK>(a, blockIdx.x, face_blocks);
 }
 
 // Face tables (once per domain, after the flags; without them, as on lattices too large for their

@@ -75,6 +75,16 @@ SIGNATURES = {
                               _P, _SZ, _P, _P]),
     "lbm_lidar_misfit_grad": (_I, [_P, ctypes.POINTER(lbm_adjoint_params), _P, _I, _F, _P, _I, _P, _I,
                                    _P, _P, _SZ, _P, _P]),
+    "lbm_batch_workspace_bytes": (_SZ, [_I]),
+    "lbm_batch_create": (_I, [_P, _I, _P, _SZ, _P, ctypes.POINTER(_P)]),
+    "lbm_batch_step": (_I, [_P, _I]),
+    "lbm_batch_capture": (_I, [_P, _I]),
+    "lbm_batch_launch": (_I, [_P]),
+    "lbm_batch_autotune": (_I, [_P, _I, _P, _P]),
+    "lbm_batch_set_shape": (_I, [_P, _I]),
+    "lbm_batch_shape": (_I, [_P]),
+    "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_batch_destroy": (None, [_P]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
     "lbm_destroy": (None, [_P]),
 }
@@ -461,6 +471,67 @@ def lidar_misfit(p, problem: LidarProblem):
     except NameError:
         fn = _LidarMisfit = _autograd_function()
     return fn.apply(p, problem)
+
+
+BATCH_SHAPES = ("4 blocks/SM, given order", "3 blocks/SM, given order", "4 blocks/SM, largest first",
+                "3 blocks/SM, largest first", "one launch per member")
+
+
+def _bcheck(status: int, batch=None):
+    if status != 0:
+        msg = load(False).lbm_batch_last_error(batch).decode() if batch else ""
+        raise LbmError(status, msg)
+
+
+class Batch:
+    """Several ``Domain`` objects advanced together (``lbm_batch_*`` in ``lbm.h``): one launch per
+    step over all members, CUDA-graph replay, launch shape by ``autotune``."""
+
+    def __init__(self, domains, stream=None):
+        import torch
+        self.domains = list(domains)
+        n = len(self.domains)
+        nbytes = load().lbm_batch_workspace_bytes(n)
+        if nbytes == 0:
+            raise LbmError(-1, "invalid batch size")
+        dev = self.domains[0].device
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else self.domains[0].stream
+        arr = (_P * n)(*[d.dom for d in self.domains])
+        out = _P()
+        _bcheck(load().lbm_batch_create(arr, n, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream,
+                                        ctypes.byref(out)))
+        self.b = out
+
+    def __del__(self):
+        b = getattr(self, "b", None)
+        if b:
+            load(False).lbm_batch_destroy(b)
+            self.b = None
+
+    def step(self, n: int = 1):
+        _bcheck(load().lbm_batch_step(self.b, int(n)), self.b)
+
+    def capture(self, n: int):
+        _bcheck(load().lbm_batch_capture(self.b, int(n)), self.b)
+
+    def launch(self):
+        _bcheck(load().lbm_batch_launch(self.b), self.b)
+
+    def autotune(self, trial_steps: int = 20):
+        """(chosen shape, ms per step of every shape)."""
+        choice = ctypes.c_int()
+        ms = (ctypes.c_float * len(BATCH_SHAPES))()
+        _bcheck(load().lbm_batch_autotune(self.b, int(trial_steps), ctypes.byref(choice), ms), self.b)
+        return choice.value, list(ms)
+
+    @property
+    def shape(self) -> int:
+        return load().lbm_batch_shape(self.b)
+
+    @shape.setter
+    def shape(self, s: int):
+        _bcheck(load().lbm_batch_set_shape(self.b, int(s)), self.b)
 
 
 def glups(cells: int, steps: int, seconds: float) -> float:

@@ -302,3 +302,39 @@ def assimilation_case(nx: int = 128, ny: int = 128, nz: int = 48, seed: int = 4,
                 meta={"seed": seed, **info})
     return Assimilation(case, L, speed, theta, guess_scale * speed, theta + guess_dtheta, cols,
                         heights, nsteps, n_avg, checkpoint_every)
+
+
+# ----------------------------------------------------------------------------- ensembles
+def ensemble_cases(nx: int = 256, ny: int = 256, nz: int = 64, seed: int = 3, n_dir: int = 16,
+                   u_refs=(0.04, 0.07), tau: float = 0.505, cs: float = 0.16, z_ref: float = 60.0,
+                   alpha: float = 0.25) -> list:
+    """Wind-rose ensemble on one synthetic city: n_dir inflow directions 0, 360/n_dir, ... degrees
+    times the reference speeds u_refs (power law, alpha 0.25, z_ref 60); faces follow each
+    direction.  Members start from the profile (no noise)."""
+    solid, info = city_mask(nx, ny, nz, seed)
+    out = []
+    for k in range(n_dir):
+        theta = math.radians(360.0 * k / n_dir)
+        for u in u_refs:
+            speed = power_law_levels(nz, u, z_ref, alpha)
+            out.append(Case(f"ens{nx}x{ny}x{nz}_d{k}_u{u}", solid, faces_for_direction(theta), tau, cs,
+                            speed, theta, meta={"seed": seed, **info}))
+    return out
+
+
+UNEVEN_SIZES = ((96, 96, 32), (128, 96, 32), (160, 128, 48), (192, 160, 48), (224, 128, 64),
+                (256, 192, 64), (288, 160, 64), (320, 192, 64))
+
+
+def uneven_cases(sizes=UNEVEN_SIZES, seed: int = 10, tau: float = 0.505, cs: float = 0.16,
+                 u_ref: float = 0.06, z_ref: float = 60.0, alpha: float = 0.25) -> list:
+    """Domains of uneven size (96x96x32 .. 320x192x64 by default), each its own seeded city and
+    seeded inflow direction, power-law inflow; members start from the profile."""
+    out = []
+    for k, (nx, ny, nz) in enumerate(sizes):
+        solid, info = city_mask(nx, ny, nz, seed + k)
+        theta = direction_from_seed(seed + k)
+        speed = power_law_levels(nz, u_ref, z_ref, alpha)
+        out.append(Case(f"uneven{nx}x{ny}x{nz}", solid, faces_for_direction(theta), tau, cs, speed, theta,
+                        meta={"seed": seed + k, **info}))
+    return out

@@ -186,3 +186,10 @@ def test_ctypes_structs_match_the_c_layout(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
+
+
+def test_batch_workspace_bytes(lib):
+    assert lbm.load(False).lbm_batch_workspace_bytes(0) == 0
+    assert lbm.load(False).lbm_batch_workspace_bytes(5000) == 0
+    small, big = lbm.load(False).lbm_batch_workspace_bytes(1), lbm.load(False).lbm_batch_workspace_bytes(40)
+    assert 0 < small < big and big % 256 == 0

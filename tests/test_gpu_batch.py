@@ -1,0 +1,123 @@
+"""Batched ensembles (lbm_batch_*): one launch per step over several domains of uneven size and
+face sets must compute exactly what lbm_step computes on each domain (App. D step, Sec. 3
+faces); graph replay equals direct stepping; the autotuner's shapes all agree."""
+import numpy as np
+import pytest
+
+from paper_2607_04516_b300 import synth
+from gpu_common import f32
+
+pytestmark = pytest.mark.gpu
+
+
+def _members():
+    """Uneven lattices with buildings, different face sets, odd and even sizes, ragged tails."""
+    out = []
+    c = synth.city_case(nx=48, ny=40, nz=16, seed=5, noise=0.01)
+    out.append(c)
+    c = synth.city_case(nx=33, ny=26, nz=12, seed=6, dir_seed=9, noise=0.01)   # odd nx: no pairs
+    out.append(c)
+    c = synth.cube_case(nx=24, ny=20, nz=12)
+    out.append(c)
+    c = synth.random_small_case(13, 7, 6, ("outflow", "inflow", "inflow", "outflow", "noslip", "freeslip"),
+                                seed=12, solid_fraction=0.1, margin=0)
+    out.append(c)
+    return out
+
+
+def _domains(cases, store):
+    from paper_2607_04516_b300 import lbm
+    doms = []
+    for c in cases:
+        d = lbm.Domain(c.solid, c.faces, c.tau, c.cs, store, c.rho_b)
+        d.set_inflow_profile(f32(c.speed), c.theta)
+        d.init_fields(f32(c.rho0), f32(c.u0))
+        doms.append(d)
+    return doms
+
+
+def _state(doms):
+    import torch
+    torch.cuda.synchronize()
+    return [d.export_populations().cpu().numpy() for d in doms]
+
+
+TOL = {"f32": 0.0, "f16s": 0.0, "bf16s": 0.0}
+
+
+@pytest.mark.parametrize("store", ["f32", "f16s", "bf16s"])
+@pytest.mark.parametrize("nsteps", [1, 6])
+def test_batched_steps_equal_single_domain_steps(store, nsteps):
+    from paper_2607_04516_b300 import lbm
+    cases = _members()
+    ref = _domains(cases, store)
+    for d in ref:
+        d.step(nsteps)
+    want = _state(ref)
+    for shape in range(5):
+        doms = _domains(cases, store)
+        b = lbm.Batch(doms)
+        b.shape = shape
+        b.step(nsteps)
+        got = _state(doms)
+        for g, w, d in zip(got, want, doms):
+            assert d.steps_done == nsteps
+            diff = float(np.abs(g - w).max())
+            assert diff <= TOL[store], (shape, diff)
+
+
+def test_graph_replay_equals_direct_steps():
+    import torch
+    from paper_2607_04516_b300 import lbm
+    cases = _members()
+    ref = _domains(cases, "f32")
+    for d in ref:
+        d.step(8)
+    want = _state(ref)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        doms = _domains(cases, "f32")
+        b = lbm.Batch(doms, stream=stream)
+        b.capture(4)
+        assert all(d.steps_done == 0 for d in doms)
+        b.launch()
+        b.launch()
+    got = _state(doms)
+    for g, w, d in zip(got, want, doms):
+        assert d.steps_done == 8
+        assert float(np.abs(g - w).max()) == 0.0
+
+
+def test_autotune_picks_a_measured_shape_and_keeps_results():
+    from paper_2607_04516_b300 import lbm
+    cases = _members()
+    doms = _domains(cases, "f32")
+    b = lbm.Batch(doms)
+    choice, ms = b.autotune(trial_steps=4)
+    assert 0 <= choice < len(lbm.BATCH_SHAPES) and b.shape == choice
+    assert all(m > 0 for m in ms) and ms[choice] == min(ms)
+    assert all(d.steps_done == 5 * 6 for d in doms)
+    ref = _domains(cases, "f32")
+    for d in ref:
+        d.step(30 + 2)
+    b.step(2)
+    for g, w in zip(_state(doms), _state(ref)):
+        assert float(np.abs(g - w).max()) == 0.0
+
+
+def test_batch_rejects_mixed_members_and_parity():
+    from paper_2607_04516_b300 import lbm
+    cases = _members()[:2]
+    a = _domains(cases[:1], "f32")[0]
+    c = _domains(cases[1:], "f16s")[0]
+    with pytest.raises(lbm.LbmError):
+        lbm.Batch([a, c])
+    d = _domains(cases[1:], "f32")[0]
+    d.step(1)
+    with pytest.raises(lbm.LbmError):
+        lbm.Batch([a, d])
+    d.step(1)
+    b = lbm.Batch([a, d])
+    a.step(1)   # stepped outside the batch: parities differ
+    with pytest.raises(lbm.LbmError):
+        b.step(1)
