@@ -35,18 +35,35 @@ def stale() -> bool:
 def build(force: bool = False, verbose: bool = False, out: str | None = None,
           defines: tuple = ()) -> str:
     """Compile the library (to ``out`` instead of the in-tree path when given, e.g. to compare
-    launch-bound variants passed as ``defines``)."""
+    launch-bound variants passed as ``defines``): one nvcc process per source file in parallel
+    (objects in a private temporary folder), then one link."""
+    import concurrent.futures
+    import shutil
+    import tempfile
     target = out or LIB
     if out is None and not force and not stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
     tmp = target + f".tmp{os.getpid()}"
-    cmd = [nvcc, "-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-shared",
-           *[f"-D{d}" for d in defines], "-I", INCLUDE, *SOURCES, "-o", tmp]
+    flags = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
+             *[f"-D{d}" for d in defines], "-I", INCLUDE]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), flush=True)
-    subprocess.run(cmd, check=True)
+        flags.insert(0, "-Xptxas=-v")
+    objdir = tempfile.mkdtemp(prefix="lbm_build_")
+    try:
+        objs = [os.path.join(objdir, os.path.basename(src) + ".o") for src in SOURCES]
+
+        def compile_one(k):
+            cmd = [nvcc, *flags, "-c", SOURCES[k], "-o", objs[k]]
+            if verbose:
+                print(" ".join(cmd), flush=True)
+            subprocess.run(cmd, check=True)
+
+        with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+            list(ex.map(compile_one, range(len(SOURCES))))
+        subprocess.run([nvcc, *ARCH, "-shared", *objs, "-o", tmp], check=True)
+    finally:
+        shutil.rmtree(objdir, ignore_errors=True)
     os.replace(tmp, target)
     return target
 

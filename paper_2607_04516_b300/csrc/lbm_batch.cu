@@ -4,9 +4,10 @@
 //
 // The grid of a batched launch is the concatenation of the members' own grids (face blocks, then
 // lattice blocks, exactly as a single-domain launch lays them out), in a slot order the autotuner
-// may change.  A block finds its slot by binary search over the slots' first blocks, copies that
-// member's step arguments from global memory into shared memory, and runs the same block body as
-// the single-domain kernels (local_block / neighbor_block).  Members keep their own workspaces and
+// may change.  A block finds its slot by binary search over the slots' first blocks, reads that
+// member's step arguments (from the kernel's parameter space for up to 48 members, else from a copy
+// in shared memory) and runs the same block body as the single-domain kernels (local_block /
+// neighbor_block).  Members keep their own workspaces and
 // state; the batch only adds a small table of step arguments and block offsets.
 #include <cuda_runtime.h>
 
@@ -69,6 +70,37 @@ __global__ void __launch_bounds__(kBlock, MINB) k_batch_step(BatchTables t) {
     }
 }
 
+// Up to kParamMembers members: the step arguments and block tables travel in the kernel's parameter
+// space (__grid_constant__, constant bank) instead of shared memory, as in the single-domain kernels.
+constexpr int kParamMembers = 48;
+struct BatchParams {
+    StepArgs args[kParamMembers];
+    unsigned start[kParamMembers + 1];
+    int member[kParamMembers];
+    int n;
+};
+static_assert(sizeof(BatchParams) <= 32000, "kernel parameter space");
+
+template <int S, bool NEIGHBOR, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_batch_step_p(const __grid_constant__ BatchParams p) {
+    int lo = 0, hi = p.n - 1;   // last slot whose first block is <= blockIdx.x (uniform)
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.start[mid] <= blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const StepArgs &a = p.args[p.member[lo]];
+    const unsigned bid = blockIdx.x - p.start[lo];
+    if constexpr (NEIGHBOR) {
+        neighbor_block<S, false, false>(a, bid, face_blocks_of(a.nface));
+    } else if constexpr (S == LBM_F32) {
+        local_block<S, false, false>(a, bid);
+    } else {
+        if (a.pack16) local_block<S, false, true>(a, bid);
+        else local_block<S, false, false>(a, bid);
+    }
+}
+
 // blocks of a member's launch of this kind (the same as its single-domain launch)
 template <int S> unsigned member_blocks(const StepArgs &a, bool neighbor) {
     return lattice_blocks<S>(a.g.N) + (neighbor ? face_blocks_of(a.nface) : 0u);
@@ -81,21 +113,29 @@ unsigned member_blocks(int store, const StepArgs &a, bool neighbor) {
     }
 }
 
+// p: parameter-space tables (null: shared-memory tables t)
 template <int S, int MINB>
-void launch_batch_t(bool neighbor, const BatchTables &t, unsigned blocks, cudaStream_t s) {
-    if (neighbor) k_batch_step<S, true, MINB><<<blocks, kBlock, 0, s>>>(t);
-    else k_batch_step<S, false, MINB><<<blocks, kBlock, 0, s>>>(t);
+void launch_batch_t(bool neighbor, const BatchTables &t, const BatchParams *p, unsigned blocks, cudaStream_t s) {
+    if (p) {
+        if (neighbor) k_batch_step_p<S, true, MINB><<<blocks, kBlock, 0, s>>>(*p);
+        else k_batch_step_p<S, false, MINB><<<blocks, kBlock, 0, s>>>(*p);
+    } else {
+        if (neighbor) k_batch_step<S, true, MINB><<<blocks, kBlock, 0, s>>>(t);
+        else k_batch_step<S, false, MINB><<<blocks, kBlock, 0, s>>>(t);
+    }
 }
 template <int S>
-void launch_batch_s(int minb, bool neighbor, const BatchTables &t, unsigned blocks, cudaStream_t s) {
-    if (minb == 3) launch_batch_t<S, 3>(neighbor, t, blocks, s);
-    else launch_batch_t<S, 4>(neighbor, t, blocks, s);
+void launch_batch_s(int minb, bool neighbor, const BatchTables &t, const BatchParams *p, unsigned blocks,
+                    cudaStream_t s) {
+    if (minb == 3) launch_batch_t<S, 3>(neighbor, t, p, blocks, s);
+    else launch_batch_t<S, 4>(neighbor, t, p, blocks, s);
 }
-void launch_batch(int store, int minb, bool neighbor, const BatchTables &t, unsigned blocks, cudaStream_t s) {
+void launch_batch(int store, int minb, bool neighbor, const BatchTables &t, const BatchParams *p, unsigned blocks,
+                  cudaStream_t s) {
     switch (store) {
-        case LBM_F32: launch_batch_s<LBM_F32>(minb, neighbor, t, blocks, s); break;
-        case LBM_F16S: launch_batch_s<LBM_F16S>(minb, neighbor, t, blocks, s); break;
-        default: launch_batch_s<LBM_BF16S>(minb, neighbor, t, blocks, s); break;
+        case LBM_F32: launch_batch_s<LBM_F32>(minb, neighbor, t, p, blocks, s); break;
+        case LBM_F16S: launch_batch_s<LBM_F16S>(minb, neighbor, t, p, blocks, s); break;
+        default: launch_batch_s<LBM_BF16S>(minb, neighbor, t, p, blocks, s); break;
     }
 }
 
@@ -129,6 +169,7 @@ struct lbm_batch {
     BatchLayout L;
     int shape;                     // 0..kShapes-1, or kSequential
     unsigned total_nb, total_lc;   // grid sizes of the two step kinds
+    BatchParams *params[2];        // parameter-space tables (neighbour, local); null above kParamMembers
     cudaGraphExec_t graph;
     int graph_steps;
     int graph_parity;
@@ -169,6 +210,16 @@ lbm_status batch_upload(lbm_batch *b) {
     }
     b->total_nb = snb[n];
     b->total_lc = slc[n];
+    if (b->params[0]) {
+        for (int kind = 0; kind < 2; ++kind) {
+            BatchParams &P = *b->params[kind];
+            std::memset(&P, 0, sizeof(P));
+            P.n = n;
+            for (int m = 0; m < n; ++m) P.args[m] = b->args[m];
+            for (int k = 0; k <= n; ++k) P.start[k] = kind == 0 ? snb[k] : slc[k];
+            for (int k = 0; k < n; ++k) P.member[k] = order[k];
+        }
+    }
     const cudaStream_t s = b->stream;
     lbm_status st = bcuda(b, cudaMemcpyAsync(b->ws + b->L.args, b->args.data(), n * sizeof(StepArgs), cudaMemcpyHostToDevice, s), "batch upload");
     if (st == LBM_OK) st = bcuda(b, cudaMemcpyAsync(b->ws + b->L.start_nb, snb.data(), (n + 1) * sizeof(unsigned), cudaMemcpyHostToDevice, s), "batch upload");
@@ -200,12 +251,19 @@ void batch_enqueue(lbm_batch *b, int nsteps, int p) {
         BatchTables t{(const StepArgs *)(b->ws + b->L.args),
                       (const unsigned *)(b->ws + (neighbor ? b->L.start_nb : b->L.start_lc)),
                       (const int *)(b->ws + b->L.member), n};
-        launch_batch(b->store, minb, neighbor, t, neighbor ? b->total_nb : b->total_lc, b->stream);
+        launch_batch(b->store, minb, neighbor, t, b->params[neighbor ? 0 : 1], neighbor ? b->total_nb : b->total_lc,
+                     b->stream);
     }
 }
 
 void batch_advance(lbm_batch *b, int nsteps) {
     for (lbm_domain *d : b->dom) domain_advance(d, nsteps);
+}
+
+void free_batch(lbm_batch *b) {
+    delete b->params[0];
+    delete b->params[1];
+    delete b;
 }
 
 void drop_graph(lbm_batch *b) {
@@ -240,9 +298,18 @@ lbm_status lbm_batch_create(lbm_domain *const *domains, int n, void *workspace, 
     b->graph = nullptr;
     b->graph_steps = 0;
     b->graph_parity = 0;
+    b->params[0] = b->params[1] = nullptr;
+    if (n <= kParamMembers) {
+        b->params[0] = new (std::nothrow) BatchParams();
+        b->params[1] = new (std::nothrow) BatchParams();
+        if (!b->params[0] || !b->params[1]) {
+            free_batch(b);
+            return LBM_ENOMEM;
+        }
+    }
     for (int m = 0; m < n; ++m) {
         lbm_domain *d = domains[m];
-        if (!d) { delete b; return LBM_EINVAL; }
+        if (!d) { free_batch(b); return LBM_EINVAL; }
         const DomainView v = domain_view(d);
         const StepArgs &a = v.args;
         if (m == 0) b->store = v.store;
@@ -250,19 +317,19 @@ lbm_status lbm_batch_create(lbm_domain *const *domains, int n, void *workspace, 
         bad |= a.fx != 0.0f || a.fy != 0.0f || a.fz != 0.0f || a.ox != 0.0f || a.oy != 0.0f || a.oz != 0.0f;
         for (lbm_domain *e : b->dom) bad |= e == d;
         if (bad) {
-            delete b;
+            free_batch(b);
             return LBM_EINVAL;   // mixed storage, forced, turbulent-inflow or repeated members
         }
         b->dom.push_back(d);
         b->args.push_back(a);
     }
     if (batch_parity(b) < 0) {
-        delete b;
+        free_batch(b);
         return LBM_ESTATE;   // members must have taken steps of the same parity
     }
     const lbm_status st = batch_upload(b);
     if (st != LBM_OK) {
-        delete b;
+        free_batch(b);
         return st;
     }
     *out = b;
@@ -370,7 +437,7 @@ const char *lbm_batch_last_error(const lbm_batch *b) { return b ? b->err : "no b
 void lbm_batch_destroy(lbm_batch *b) {
     if (!b) return;
     drop_graph(b);
-    delete b;
+    free_batch(b);
 }
 
 }  // extern "C"
