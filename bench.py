@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--store", default="f32", choices=list(STORE_BYTES))
     ap.add_argument("--workload", default="city400", choices=list(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10,adjoint,ensemble",
+    ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10,zones,adjoint,ensemble",
                     help="extra storage kinds timed after the main measurement ('' = none)")
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--adjoint-steps", type=int, default=2000,
@@ -406,8 +406,8 @@ def run_ours(args, rank, world):
     clock_id = f"GPU-{clock_id}" if clock_id is not None and not str(clock_id).startswith("GPU-") else (
         str(clock_id) if clock_id is not None else str(local))
 
-    def build_domain(store):
-        dom = lbm.Domain(case.solid, case.faces, case.tau, case.cs, store)
+    def build_domain(store, **kw):
+        dom = lbm.Domain(case.solid, case.faces, case.tau, case.cs, store, **kw)
         dom.set_inflow_profile(case.speed.astype(np.float32), case.theta)
         dom.init_fields(None, None if case.u0 is None else case.u0.astype(np.float32))
         return dom
@@ -444,6 +444,21 @@ def run_ours(args, rank, world):
             continue
         if st == "ensemble":
             variants[st] = ensemble_leg(world)
+            continue
+        if st == "zones":
+            # FP32 with the boundary relaxation zones (Sec. 3): a top sponge 10 cells deep (rate 0.05
+            # at the top) and buffers 16 cells wide next to the open lateral faces (0.02), plus flux
+            # balancing; the zones take the general (forced) step kernels
+            d2 = build_domain("f32", sponge=(10, 0.05), buffer=(16, 0.02), flux_balance=True)
+            K2 = max(200, args.steps // 4)
+            t_ms, _, _, _, _ = time_steps(d2, K2, min(args.warmup, 200), world, None)
+            t_ms = max_over_ranks(t_ms, world)
+            g2 = weak_scaling_glups(N, K2, world, t_ms)
+            variants[st] = {"glups": g2, "vs_f32": g2 / value if args.store == "f32" else None,
+                            "ms_per_step": t_ms / K2, "sponge": [10, 0.05], "buffer": [16, 0.02],
+                            "flux_balance": list(d2.flux_balance_info())}
+            del d2
+            torch.cuda.empty_cache()
             continue
         if st in ("stg", "stg_s10"):
             # FP32 with the synthetic von Karman inflow (App. F) on the inflow faces: 64 modes,

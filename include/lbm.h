@@ -81,16 +81,38 @@ typedef struct {
     float coriolis[3];    /* rotation vector Omega^lbm (lattice units, e.g. lbm_coriolis_omega);
                              each fluid cell adds the Coriolis force 2 rho Omega^lbm x u, u = sum c f
                              / rho, to the body force of Guo's forcing (App. E); {0,0,0} = none */
+    /* Relaxation zones next to the outer faces (Sec. 3: a top sponge layer and buffer nudging toward
+     * the target boundary state next to the lateral faces).  After its collision, a fluid cell at
+     * distance d (cells) from a zone's face layer, d < width, relaxes toward the equilibrium of its
+     * own density and the profile velocity u_b(z):  f* <- f* - s (f* - f^eq(rho, u_b(z))),
+     * s = sigma ((width - d) / width)^2, the largest s where zones overlap.  Mass is kept; the
+     * velocity deviation from u_b shrinks by the factor (1 - s) per step. */
+    int sponge_top;       /* width of the zone under the top face layer (z = nz - 1); 0 = none */
+    float sponge_sigma;   /* its rate at the face layer, 0 <= sigma <= 1 */
+    int buffer_width;     /* width of the zones next to the open lateral faces (INFLOW_EQ or
+                             OUTFLOW_ZG among x-, x+, y-, y+); 0 = none */
+    float buffer_sigma;   /* their rate at the face layer, 0 <= sigma <= 1 */
+    int flux_balance;     /* 1: mass-flux consistency (Sec. 2.1, Sec. 3): every equilibrium boundary cell's
+                             velocity gets the same shift along the inward normal of the face owning
+                             it (x-, x+, y-, y+, z-, z+: the first inflow face holding the cell), the
+                             smallest uniform shift that makes the net volume inflow of all equilibrium
+                             cells zero; recomputed by lbm_set_inflow_profile.  0 = off */
 } lbm_params;
 
 /* Fill p with defaults: tau 0.52, C 0.16, rho_b 1, F32, x- inflow, x+ outflow, periodic y,
- * no-slip ground, free-slip top, no force, no rotation, no watchdog.  Returns LBM_EINVAL if p
- * is NULL. */
+ * no-slip ground, free-slip top, no force, no rotation, no watchdog, no relaxation zones, no flux
+ * balancing.  Returns LBM_EINVAL if p is NULL. */
 lbm_status lbm_params_default(lbm_params *p);
 
 /* Earth rotation in the local east-north-up frame at latitude lat_deg, in lattice units (App. E):
  * Omega^lbm = Omega dt_si (0, cos lat, sin lat) with Omega = 7.292115e-5 rad/s.  out: 3 floats. */
 lbm_status lbm_coriolis_omega(double lat_deg, double dt_si, float *out);
+
+/* Net volume inflow of the equilibrium boundary cells (sum over them of u . n_in, n_in the inward
+ * normal of the face owning the cell, one cell face of area 1 each) before and after the flux
+ * balancing of the current profile, and the normal shift applied (0 when flux_balance is off).
+ * HOST outputs, any may be NULL. */
+lbm_status lbm_flux_balance_info(const lbm_domain *d, double *before, double *after, double *shift);
 
 /* Lateral face kinds for a wind direction theta (radians, 0 = +x, counter-clockwise): a lateral
  * face is INFLOW_EQ when the wind enters through it (u . n_in > 1e-6 |u|), OUTFLOW_ZG otherwise;
@@ -262,7 +284,8 @@ lbm_status lbm_stg_reference(const lbm_domain *d, double *u_ref, double *e_c, in
  * and App. A; these calls give the gradient of the same fit, so the inflow can be recovered by
  * gradient descent.)
  *
- * Forward model (FP32 storage, no body force, no rotation, synthetic inflow off):
+ * Forward model (FP32 storage, no body force, no rotation, no relaxation zones, no flux balancing,
+ * synthetic inflow off):
  *   1. lbm_set_inflow_profile(speed, L, theta) and lbm_init_fields(NULL, NULL): every non-solid
  *      cell starts at f^eq of the profile velocity u_b(z) (rho = 1, equilibrium cells rho_b);
  *   2. n_steps fused steps (lbm_step); the domain is left at step n_steps;
@@ -320,7 +343,8 @@ lbm_status lbm_lidar_misfit_grad(lbm_domain *d, const lbm_adjoint_params *p, con
  * studies iterate over.)
  *
  * Members keep their own workspaces, profiles and state; every member must use the same storage
- * kind, have no body force, no rotation and no synthetic inflow, and have taken steps of the same
+ * kind, have no body force, no rotation, no relaxation zones and no synthetic inflow, and have taken
+ * steps of the same
  * parity (they then advance in lockstep: lbm_steps_done grows by the same amount on each).  A
  * batched step computes exactly what lbm_step computes on each member.
  * --------------------------------------------------------------------------------------------- */

@@ -540,6 +540,8 @@ lbm_status lidar_forward(lbm_domain *d, const lbm_adjoint_params *p, const float
         return domain_fail(d, LBM_EINVAL, "lidar misfit: body forces and rotation are not supported");
     for (int f = 0; f < 6; ++f)
         if (a0.ueq[f]) return domain_fail(d, LBM_EINVAL, "lidar misfit: switch the synthetic inflow off first");
+    if (a0.sponge_top > 0 || a0.buffer_faces != 0 || a0.flux_balance)
+        return domain_fail(d, LBM_EINVAL, "lidar misfit: relaxation zones and flux balancing are not supported");
     if (!ij || !k || ncol < 1 || nh < 1) return domain_fail(d, LBM_EINVAL, "lidar misfit: need >= 1 column and height");
     if ((long long)ncol * nh > (1 << 20)) return domain_fail(d, LBM_EINVAL, "lidar misfit: more than 2^20 samples");
     if (!ws || ((uintptr_t)ws % 256)) return domain_fail(d, LBM_EINVAL, "lidar misfit: workspace NULL or not 256-byte aligned");

@@ -315,6 +315,7 @@ lbm_status lbm_batch_create(lbm_domain *const *domains, int n, void *workspace, 
         if (m == 0) b->store = v.store;
         bool bad = v.store != b->store || domain_stg_on(d);
         bad |= a.fx != 0.0f || a.fy != 0.0f || a.fz != 0.0f || a.ox != 0.0f || a.oy != 0.0f || a.oz != 0.0f;
+        bad |= a.sponge_top > 0 || a.buffer_faces != 0;
         for (lbm_domain *e : b->dom) bad |= e == d;
         if (bad) {
             free_batch(b);

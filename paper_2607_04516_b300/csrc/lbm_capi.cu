@@ -55,6 +55,10 @@ const char *check_args(int nx, int ny, int nz, const lbm_params *p) {
         if (lo != LBM_FACE_PERIODIC && n[a] < 2) return "non-periodic axes need at least 2 cells";
     }
     if (p->watchdog_every < 0) return "watchdog_every must be >= 0";
+    if (p->sponge_top < 0 || p->buffer_width < 0) return "relaxation zone widths must be >= 0";
+    if (!(p->sponge_sigma >= 0.0f && p->sponge_sigma <= 1.0f)) return "sponge_sigma must be in [0, 1]";
+    if (!(p->buffer_sigma >= 0.0f && p->buffer_sigma <= 1.0f)) return "buffer_sigma must be in [0, 1]";
+    if (p->flux_balance != 0 && p->flux_balance != 1) return "flux_balance must be 0 or 1";
     return nullptr;
 }
 
@@ -112,6 +116,7 @@ struct lbm_domain {
     std::vector<float> ub_host;  // expanded profile staging
     std::vector<uint8_t> face_solid[6];   // solid mask on each face plane (n1 fastest)
     StgState stg;                // synthetic inflow turbulence (App. F)
+    double flux_before, flux_after, flux_shift;   // flux balancing of the current profile
     char err[512];
 };
 
@@ -163,6 +168,16 @@ StepArgs args_of(const lbm_domain *d) {
     a.pack16 = (d->p.store != LBM_F32 && d->N % 2 == 0 && d->nx % 2 == 0) ? 1 : 0;
     a.ftab = d->L.ngen ? (const uint32_t *)(d->ws + d->L.ftab) : nullptr;
     a.ngen = d->L.ngen;
+    a.sponge_top = d->p.sponge_sigma > 0.0f ? d->p.sponge_top : 0;
+    a.sponge_sigma = d->p.sponge_sigma;
+    a.buffer_width = d->p.buffer_width;
+    a.buffer_sigma = d->p.buffer_sigma;
+    a.buffer_faces = 0;
+    if (d->p.buffer_width > 0 && d->p.buffer_sigma > 0.0f)
+        for (int k = 0; k < 4; ++k)
+            if (d->p.face[k] == LBM_FACE_INFLOW_EQ || d->p.face[k] == LBM_FACE_OUTFLOW_ZG) a.buffer_faces |= 1 << k;
+    a.flux_balance = d->p.flux_balance;
+    a.flux_shift = d->p.flux_balance ? (float)d->flux_shift : 0.0f;
     if (d->stg.on && d->stg.valid) {
         const StgState &s = d->stg;
         for (int k = 0; k < s.L.nfaces; ++k) {
@@ -185,10 +200,69 @@ lbm_status stg_rebuild(lbm_domain *d) {
                                          cudaMemcpyHostToDevice, d->stream), "stg table upload");
 }
 
+// The step needs the general (forced) kernels: a body force, rotation or relaxation zones.
 bool has_force(const lbm_domain *d) {
     for (int k = 0; k < 3; ++k)
         if (d->p.force[k] != 0.0f || d->p.coriolis[k] != 0.0f) return true;
-    return false;
+    const StepArgs a = args_of(d);
+    return a.sponge_top > 0 || a.buffer_faces != 0;
+}
+
+// Flux balancing (Sec. 2.1): net volume inflow of the equilibrium cells of the profile, from the
+// host copies of the profile and of the face planes' solid masks, and the uniform inward normal
+// shift that cancels it (the least-squares smallest correction: the same on every cell).
+void flux_balance_update(lbm_domain *d) {
+    d->flux_before = d->flux_after = d->flux_shift = 0.0;
+    const int n[3] = {d->nx, d->ny, d->nz};
+    double phi = 0.0;
+    long long cells = 0;
+    for (int k = 0; k < 6; ++k) {
+        if (d->p.face[k] != LBM_FACE_INFLOW_EQ) continue;
+        const int a = k / 2, hi = k & 1;
+        const int n1 = a == 0 ? n[1] : n[0], n2 = a == 2 ? n[1] : n[2];
+        const double sgn = hi ? -1.0 : 1.0;
+        for (int j = 0; j < n2; ++j)
+            for (int i = 0; i < n1; ++i) {
+                if (d->face_solid[k][(size_t)i + (size_t)n1 * j]) continue;
+                const int p[3] = {a == 0 ? (hi ? n[0] - 1 : 0) : i, a == 1 ? (hi ? n[1] - 1 : 0) : (a == 0 ? i : j),
+                                  a == 2 ? (hi ? n[2] - 1 : 0) : j};
+                // owned by the first inflow face (x-, x+, y-, y+, z-, z+) holding the cell
+                int owner = -1;
+                for (int q = 0; q < 6 && owner < 0; ++q)
+                    if (d->p.face[q] == LBM_FACE_INFLOW_EQ && p[q / 2] == ((q & 1) ? n[q / 2] - 1 : 0)) owner = q;
+                if (owner != k) continue;
+                phi += sgn * (double)d->ub_host[3 * p[2] + a];
+                ++cells;
+            }
+    }
+    d->flux_before = phi;
+    if (!d->p.flux_balance || cells == 0) {
+        d->flux_after = phi;
+        return;
+    }
+    d->flux_shift = -phi / (double)cells;
+    // what the kernels apply: the profile and the shift in FP32
+    const float sh = (float)d->flux_shift;
+    double after = 0.0;
+    for (int k = 0; k < 6; ++k) {
+        if (d->p.face[k] != LBM_FACE_INFLOW_EQ) continue;
+        const int a = k / 2, hi = k & 1;
+        const int n1 = a == 0 ? n[1] : n[0], n2 = a == 2 ? n[1] : n[2];
+        const double sgn = hi ? -1.0 : 1.0;
+        for (int j = 0; j < n2; ++j)
+            for (int i = 0; i < n1; ++i) {
+                if (d->face_solid[k][(size_t)i + (size_t)n1 * j]) continue;
+                const int p[3] = {a == 0 ? (hi ? n[0] - 1 : 0) : i, a == 1 ? (hi ? n[1] - 1 : 0) : (a == 0 ? i : j),
+                                  a == 2 ? (hi ? n[2] - 1 : 0) : j};
+                int owner = -1;
+                for (int q = 0; q < 6 && owner < 0; ++q)
+                    if (d->p.face[q] == LBM_FACE_INFLOW_EQ && p[q / 2] == ((q & 1) ? n[q / 2] - 1 : 0)) owner = q;
+                if (owner != k) continue;
+                const float u = d->ub_host[3 * p[2] + a] + (float)(sgn * sh);
+                after += sgn * (double)u;
+            }
+    }
+    d->flux_after = after;
 }
 
 }  // namespace
@@ -285,6 +359,7 @@ lbm_status lbm_create_domain(const uint8_t *solid, int nx, int ny, int nz, const
     d->t = 0;
     d->err[0] = 0;
     d->ub_host.assign((size_t)nz * 3, 0.0f);
+    d->flux_before = d->flux_after = d->flux_shift = 0.0;
     for (int k = 0; k < 6; ++k) {
         // face plane k: (y, z), (x, z) or (x, y), first index fastest
         const int a = k / 2, hi = k & 1;
@@ -346,6 +421,7 @@ lbm_status lbm_set_inflow_profile(lbm_domain *d, const float *speed, int L, floa
     }
     lbm_status st = cuda_check(d, cudaMemcpyAsync(d->ws + d->L.ub, d->ub_host.data(), (size_t)nz * 3 * sizeof(float),
                                                   cudaMemcpyHostToDevice, d->stream), "profile upload");
+    flux_balance_update(d);
     if (st == LBM_OK && d->stg.on) st = stg_rebuild(d);
     return st;
 }
@@ -414,6 +490,14 @@ lbm_status lbm_step(lbm_domain *d, int n) {
 }
 
 long long lbm_steps_done(const lbm_domain *d) { return d ? d->t : -1; }
+
+lbm_status lbm_flux_balance_info(const lbm_domain *d, double *before, double *after, double *shift) {
+    if (!d) return LBM_EINVAL;
+    if (before) *before = d->flux_before;
+    if (after) *after = d->flux_after;
+    if (shift) *shift = d->p.flux_balance ? d->flux_shift : 0.0;
+    return LBM_OK;
+}
 
 lbm_status lbm_sample_columns(lbm_domain *d, const int *ij, int ncol, const int *k, int nh, float *out) {
     if (!d) return LBM_EINVAL;

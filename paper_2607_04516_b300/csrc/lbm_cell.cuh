@@ -125,6 +125,7 @@ LBM_HD void cell_local(const StepArgs &a, int n) {
         eq_cell_g(a, n, g);
     } else {
         collide<FORCE>(g, a);
+        if (FORCE) nudge(a, n, g);   // relaxation zones ride on the general (forced) path
     }
     if (fl & F_REDIR) {
         const unsigned nb = a.info[n] >> 8;
@@ -164,6 +165,7 @@ LBM_HD void cell_neighbor_interior(const StepArgs &a, int n) {
     if (fl & (F_SOLID | F_FACE)) return;
     const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
     collide<FORCE>(g, a);
+    if (FORCE) nudge(a, n, g);   // relaxation zones ride on the general (forced) path
     if (nb) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -210,6 +212,7 @@ LBM_HD void cell_neighbor_zlayer(const StepArgs &a, int n, uint8_t fl, bool top)
         g[i] = Cd::dec(p[idx]);
     }
     collide<FORCE>(g, a);
+    if (FORCE) nudge(a, n, g);   // relaxation zones ride on the general (forced) path
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         T *p;
@@ -253,6 +256,7 @@ LBM_HD void cell_neighbor_face(const StepArgs &a, uint8_t fl, int x, int y, int 
             g[i] = Cd::dec(base[l.idx]);
         }
         collide<FORCE>(g, a);
+        if (FORCE) nudge(a, cell_of(a.g, x, y, z), g);   // relaxation zones ride on the general (forced) path
     }
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
@@ -346,6 +350,7 @@ LBM_HD bool cell_neighbor_table(const StepArgs &a, int t) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) g[i] = Cd::dec(f[e[i]]);
         collide<FORCE>(g, a);
+        if (FORCE) nudge(a, (long long)(head & kFtCell), g);   // relaxation zones ride on the general (forced) path
     }
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
@@ -408,6 +413,7 @@ LBM_HD void cell2_local(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) g[i] = Cd::template dec_bits_s<LS>(c ? pk[i] >> 16 : pk[i] & 0xffffu);
             collide<FORCE, kPairs16, LS>(g, a);
+            if (FORCE) nudge(a, n, g);   // relaxation zones ride on the general (forced) path
         }
         store_local_one<S, FORCE>(a, n, fl, g);
     }
@@ -435,6 +441,7 @@ LBM_HD void cell2_neighbor_interior(const StepArgs &a, int n0, int n1, bool v0, 
 #pragma unroll
         for (int i = 0; i < Q; ++i) g[i] = Cd::template dec_bits_s<LS>(c ? pk[i] >> 16 : pk[i] & 0xffffu);
         collide<FORCE, kPairs16, LS>(g, a);
+        if (FORCE) nudge(a, n, g);   // relaxation zones ride on the general (forced) path
         const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
         if (nb) {
 #pragma unroll
@@ -478,6 +485,7 @@ LBM_HD void cellp_local(const StepArgs &a, int n0) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) g[i] = Cd::template dec_bits_s<LS>(c ? pk[i] >> 16 : pk[i] & 0xffffu);
             collide<FORCE, kPairs16, LS>(g, a);
+            if (FORCE) nudge(a, n0 + c, g);   // relaxation zones ride on the general (forced) path
         }
         if (fl & F_ZG) {
             int x, y, z;
@@ -536,6 +544,7 @@ LBM_HD void cellp_neighbor_interior(const StepArgs &a, int n0) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) g[i] = Cd::template dec_bits_s<LS>(c ? pk[i] >> 16 : pk[i] & 0xffffu);
         collide<FORCE, kPairs16, LS>(g, a);
+        if (FORCE) nudge(a, c ? n1 : n0, g);   // relaxation zones ride on the general (forced) path
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const uint32_t bits = Cd::template enc_bits_s<LS>(g[i]);
@@ -686,6 +695,78 @@ LBM_HD void cell2_neighbor_interior_dual(const StepArgs &a, int n0, int n1, bool
     cell2_neighbor_interior_dual_body<S>(a, n0, n1, pk, v0 ? a.flags[n0] : F_SOLID, v1 ? a.flags[n1] : F_SOLID);
 }
 
+// ---------------------------------------------------------------- FP32 storage, two cells at once
+// Unforced FP32 steps with two cells per thread (n0 and n0 + 256, so every warp access stays 32
+// consecutive cells of a plane): both cells' loads are issued before either is computed, and both
+// go through one collide2 (FP32x2 instructions).  Stores per cell, as in the one-cell kernels.
+
+LBM_HD void cell2_local_dual_f32(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
+    float *const *P = (float *const *)a.plane;
+    float2 g[Q];   // loaded before the flags are known (n1 may be past N: guard region)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = make_float2(ld_early_f32(P[i] + n0), ld_early_f32(P[i] + n1));
+    const uint8_t f0 = v0 ? a.flags[n0] : F_SOLID, f1 = v1 ? a.flags[n1] : F_SOLID;
+    if ((f0 & f1) & F_SOLID) return;
+    collide2<0>(g, a);
+    if ((f0 | f1) & F_EQ) eq_lanes<0>(a, n0, n1, f0, f1, g);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const uint8_t fl = c ? f1 : f0;
+        if (fl & F_SOLID) continue;
+        const int n = c ? n1 : n0;
+        if (fl & F_REDIR) {
+            const unsigned nb = a.info[n] >> 8;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const bool bb = (nb >> i) & 1u;
+                (bb ? P[i] : P[opp(i)])[bb ? n + a.off[i] : n] = c ? g[i].y : g[i].x;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) P[opp(i)][n] = c ? g[i].y : g[i].x;
+        }
+        if (fl & F_ZG) {
+            float gc[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) gc[i] = c ? g[i].y : g[i].x;
+            int x, y, z;
+            cell_coords(a.g, n, x, y, z);
+            store_side<float>(a.g, a.side, x, y, z, gc, [](float v) { return v; });
+        }
+    }
+}
+
+LBM_HD void cell2_neighbor_interior_dual_f32(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
+    float *const *P = (float *const *)a.plane;
+    float2 g[Q];   // loaded before the flags are known (guard region after the planes)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float *p = P[opp(i)] - a.off[i];
+        g[i] = make_float2(ld_early_f32(p + n0), ld_early_f32(p + n1));
+    }
+    const uint8_t f0 = v0 ? a.flags[n0] : F_SOLID, f1 = v1 ? a.flags[n1] : F_SOLID;
+    const bool l0 = !(f0 & (F_SOLID | F_FACE)), l1 = !(f1 & (F_SOLID | F_FACE));
+    if (!l0 && !l1) return;
+    collide2<0>(g, a);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!(c ? l1 : l0)) continue;
+        const int n = c ? n1 : n0;
+        const uint8_t fl = c ? f1 : f0;
+        const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
+        if (nb) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const bool bb = (nb >> i) & 1u;
+                (bb ? P[opp(i)] : P[i])[bb ? n : n + a.off[i]] = c ? g[i].y : g[i].x;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) P[i][n + a.off[i]] = c ? g[i].y : g[i].x;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- post-collision readback
 // Shifted post-collision populations of a non-solid cell n in the current layout.
 template <int S>
@@ -785,8 +866,15 @@ constexpr int kBlock = 256;
 #endif
 constexpr bool kDual16 = LBM_DUAL16 != 0;
 
-// cells per thread of the lattice blocks: one for FP32 storage, two for 16-bit storage
-template <int S> __host__ __device__ constexpr int cells_per_thread() { return S == LBM_F32 ? 1 : 2; }
+// FP32 storage, unforced steps: two cells per thread through collide2 (1), or one cell per thread
+// (0); chosen by measurement on B300
+#ifndef LBM_DUAL32
+#define LBM_DUAL32 0
+#endif
+constexpr bool kDual32 = LBM_DUAL32 != 0;
+
+// cells per thread of the lattice blocks: two (16-bit storage, and FP32 with kDual32), else one
+template <int S> __host__ __device__ constexpr int cells_per_thread() { return (S == LBM_F32 && !kDual32) ? 1 : 2; }
 
 // lattice blocks of a launch over N cells
 template <int S> __host__ __device__ inline unsigned lattice_blocks(long long N) {
@@ -797,7 +885,16 @@ __host__ __device__ inline unsigned face_blocks_of(long long nface) { return (un
 
 template <int S, bool FORCE, bool PACK>
 __device__ __forceinline__ void local_block(const StepArgs &a, unsigned bid) {
-    if constexpr (cells_per_thread<S>() == 1) {
+    if constexpr (S == LBM_F32 && cells_per_thread<S>() == 2) {
+        const int n0 = (int)(bid * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
+        if (n0 >= a.g.N) return;
+        if constexpr (!FORCE) {
+            cell2_local_dual_f32(a, n0, n1, true, n1 < a.g.N);
+        } else {
+            cell_local<S, true>(a, n0);
+            if (n1 < a.g.N) cell_local<S, true>(a, n1);
+        }
+    } else if constexpr (cells_per_thread<S>() == 1) {
         const int n = (int)(bid * kBlock + threadIdx.x);
         if (n >= a.g.N) return;
         cell_local<S, FORCE>(a, n);
@@ -816,7 +913,16 @@ __device__ __forceinline__ void local_block(const StepArgs &a, unsigned bid) {
 template <int S, bool FORCE, bool PACK>
 __device__ __forceinline__ void neighbor_block(const StepArgs &a, unsigned bid, unsigned face_blocks) {
     if (bid >= face_blocks) {
-        if constexpr (cells_per_thread<S>() == 1) {
+        if constexpr (S == LBM_F32 && cells_per_thread<S>() == 2) {
+            const int n0 = (int)((bid - face_blocks) * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
+            if (n0 >= a.g.N) return;
+            if constexpr (!FORCE) {
+                cell2_neighbor_interior_dual_f32(a, n0, n1, true, n1 < a.g.N);
+            } else {
+                cell_neighbor_interior<S, true>(a, n0);
+                if (n1 < a.g.N) cell_neighbor_interior<S, true>(a, n1);
+            }
+        } else if constexpr (cells_per_thread<S>() == 1) {
             const int n = (int)((bid - face_blocks) * kBlock + threadIdx.x);
             if (n >= a.g.N) return;
             cell_neighbor_interior<S, FORCE>(a, n);

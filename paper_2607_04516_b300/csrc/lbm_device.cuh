@@ -222,6 +222,13 @@ struct StepArgs {
     float ueq_alpha;            // U = (1 - alpha) ueq + alpha ueq_next
     const uint32_t *ftab;       // face tables of the first ngen face cells (null: every face cell
     int ngen;                   // takes the general resolution); layout in lbm_cell.cuh
+    int sponge_top;             // relaxation zones (see nudge): top width, its rate,
+    float sponge_sigma;
+    int buffer_width;           // lateral width and rate, and the lateral faces that have a zone
+    float buffer_sigma;         // (bit k: face k of x-, x+, y-, y+)
+    int buffer_faces;
+    float flux_shift;           // flux balancing: inward normal shift of equilibrium velocities
+    int flux_balance;           // flux balancing on (the shift follows the profile)
 };
 
 // Face tables (see cell_face_table): 32-bit storage-element codes per face cell
@@ -729,6 +736,27 @@ LBM_HD void cell_coords(const Geo &G, long long n, int &x, int &y, int &z) {
     x = (int)(r - (long long)y * G.sy);
 }
 
+// Inward unit normal of the face owning an equilibrium cell for the flux balancing: the first
+// INFLOW_EQ face (x-, x+, y-, y+, z-, z+) whose layer holds the cell; -1 if none.
+LBM_HD int flux_owner(const Geo &G, int x, int y, int z) {
+    const int p[3] = {x, y, z};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int a = k >> 1;
+        if (G.face[k] == LBM_FACE_INFLOW_EQ && p[a] == ((k & 1) ? dim(G, a) - 1 : 0)) return k;
+    }
+    return -1;
+}
+LBM_HD void add_flux_shift(const StepArgs &a, int x, int y, int z, float &ux, float &uy, float &uz) {
+    if (a.flux_shift == 0.0f) return;
+    const int k = flux_owner(a.g, x, y, z);
+    if (k < 0) return;
+    const float v = (k & 1) ? -a.flux_shift : a.flux_shift;
+    if (k < 2) ux += v;
+    else if (k < 4) uy += v;
+    else uz += v;
+}
+
 // Velocity of the equilibrium cell (x, y, z).  With synthetic inflow turbulence on, a cell on an
 // inflow face takes the value in the plane of the first inflow face holding it, in the order
 // x-, x+, y-, y+, z+ (each boundary cell belongs to one face, App. F); a cell on none of them (an
@@ -755,12 +783,47 @@ LBM_HD void eq_velocity(const StepArgs &a, int x, int y, int z, float &ux, float
     } else {
         ux = a.ub[3 * z]; uy = a.ub[3 * z + 1]; uz = a.ub[3 * z + 2];
     }
+    add_flux_shift(a, x, y, z, ux, uy, uz);
 }
 
 LBM_HD void eq_velocity(const StepArgs &a, long long n, float &ux, float &uy, float &uz) {
     int x, y, z;
     cell_coords(a.g, n, x, y, z);
     eq_velocity(a, x, y, z, ux, uy, uz);
+}
+
+// Relaxation zones next to the top and the open lateral faces (Sec. 3): after its collision the fluid
+// cell n relaxes toward f^eq(rho, u_b(z)) with the largest zone rate s = sigma ((w - d)/w)^2 over the
+// zones whose face layer is d < w cells away.  g: shifted post-collision populations (in/out).
+LBM_HD void nudge(const StepArgs &a, long long n, float (&g)[Q]) {
+    if (a.sponge_top <= 0 && a.buffer_faces == 0) return;
+    int x, y, z;
+    cell_coords(a.g, n, x, y, z);
+    float s = 0.0f;
+    if (a.sponge_top > 0) {
+        const int d = a.g.nz - 1 - z;
+        if (d < a.sponge_top) {
+            const float r = (float)(a.sponge_top - d) / (float)a.sponge_top;
+            s = fmaxf(s, a.sponge_sigma * r * r);
+        }
+    }
+    if (a.buffer_faces) {
+        const int dist[4] = {x, a.g.nx - 1 - x, y, a.g.ny - 1 - y};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!((a.buffer_faces >> k) & 1) || dist[k] >= a.buffer_width) continue;
+            const float r = (float)(a.buffer_width - dist[k]) / (float)a.buffer_width;
+            s = fmaxf(s, a.buffer_sigma * r * r);
+        }
+    }
+    if (s <= 0.0f) return;
+    float drho = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) drho += g[i];
+    float geq[Q];
+    equilibrium_shifted(drho, a.ub[3 * z], a.ub[3 * z + 1], a.ub[3 * z + 2], geq);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = fmaf(-s, g[i] - geq[i], g[i]);
 }
 
 // Shifted equilibrium of an equilibrium cell.

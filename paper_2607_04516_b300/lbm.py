@@ -32,7 +32,10 @@ class LbmError(RuntimeError):
 class lbm_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("cs_smag", ctypes.c_float), ("rho_b", ctypes.c_float),
                 ("store", ctypes.c_int), ("face", ctypes.c_int * 6), ("force", ctypes.c_float * 3),
-                ("watchdog_every", ctypes.c_int), ("coriolis", ctypes.c_float * 3)]
+                ("watchdog_every", ctypes.c_int), ("coriolis", ctypes.c_float * 3),
+                ("sponge_top", ctypes.c_int), ("sponge_sigma", ctypes.c_float),
+                ("buffer_width", ctypes.c_int), ("buffer_sigma", ctypes.c_float),
+                ("flux_balance", ctypes.c_int)]
 
 
 class lbm_stg_params(ctypes.Structure):
@@ -59,6 +62,7 @@ SIGNATURES = {
     "lbm_init_fields": (_I, [_P, _P, _P]),
     "lbm_step": (_I, [_P, _I]),
     "lbm_steps_done": (_LL, [_P]),
+    "lbm_flux_balance_info": (_I, [_P, _P, _P, _P]),
     "lbm_sample_columns": (_I, [_P, _P, _I, _P, _I, _P]),
     "lbm_macroscopic": (_I, [_P, _P, _P]),
     "lbm_export_populations": (_I, [_P, _P]),
@@ -129,7 +133,8 @@ def _check(status: int, dom=None):
 
 
 def make_params(faces, tau=0.52, cs=0.16, store="f32", rho_b=1.0, force=None, watchdog_every=0,
-                coriolis=None):
+                coriolis=None, sponge=None, buffer=None, flux_balance=False):
+    """``sponge`` / ``buffer``: (width, sigma) of the top / lateral relaxation zones, or None."""
     p = lbm_params()
     load(False).lbm_params_default(ctypes.byref(p))
     p.tau = tau
@@ -143,6 +148,11 @@ def make_params(faces, tau=0.52, cs=0.16, store="f32", rho_b=1.0, force=None, wa
     p.watchdog_every = watchdog_every
     for k in range(3):
         p.coriolis[k] = 0.0 if coriolis is None else float(coriolis[k])
+    if sponge is not None:
+        p.sponge_top, p.sponge_sigma = int(sponge[0]), float(sponge[1])
+    if buffer is not None:
+        p.buffer_width, p.buffer_sigma = int(buffer[0]), float(buffer[1])
+    p.flux_balance = int(bool(flux_balance))
     return p
 
 
@@ -307,7 +317,8 @@ class Domain:
 
     def __init__(self, solid: np.ndarray, faces, tau: float = 0.52, cs: float = 0.16,
                  store: str = "f32", rho_b: float = 1.0, force=None, watchdog_every: int = 0,
-                 device: str = "cuda", stream=None, coriolis=None):
+                 device: str = "cuda", stream=None, coriolis=None, sponge=None, buffer=None,
+                 flux_balance: bool = False):
         import torch
         load()
         self.shape = tuple(solid.shape)
@@ -315,7 +326,8 @@ class Domain:
         self.N = nx * ny * nz
         self.faces = tuple(faces)
         self.store = store
-        self.params = make_params(faces, tau, cs, store, rho_b, force, watchdog_every, coriolis)
+        self.params = make_params(faces, tau, cs, store, rho_b, force, watchdog_every, coriolis,
+                                  sponge, buffer, flux_balance)
         nbytes = lbm_workspace_bytes(nx, ny, nz, self.params)
         if nbytes == 0:
             raise LbmError(-1, "invalid domain arguments")
@@ -350,6 +362,12 @@ class Domain:
     @property
     def steps_done(self) -> int:
         return lbm_steps_done(self.dom)
+
+    def flux_balance_info(self):
+        """(net inflow before, after, normal shift) of the equilibrium cells' profile velocities."""
+        v = [ctypes.c_double() for _ in range(3)]
+        _check(load(False).lbm_flux_balance_info(self.dom, *[ctypes.byref(x) for x in v]), self.dom)
+        return tuple(x.value for x in v)
 
     def macroscopic(self):
         import torch

@@ -1,0 +1,76 @@
+"""GPU parity of the boundary relaxation zones (top sponge, lateral buffers) and the flux balancing
+against the FP64 oracle (oracle/zones.py; Sec. 3 boundary paragraph, Sec. 2.1 flux consistency)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from oracle import zones
+from paper_2607_04516_b300 import synth
+from gpu_common import TOL_U, f32, f64_of_f32, lib_to_oracle_order, oracle_inputs, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+FACE_SETS = [
+    ("inflow", "outflow", "periodic", "periodic", "noslip", "freeslip"),
+    ("outflow", "inflow", "inflow", "outflow", "noslip", "freeslip"),
+    ("inflow", "outflow", "outflow", "inflow", "noslip", "outflow"),
+    ("inflow", "inflow", "inflow", "outflow", "noslip", "inflow"),
+]
+
+
+def _gpu(case, store="f32", **kw):
+    from paper_2607_04516_b300 import lbm
+    d = lbm.Domain(case.solid, case.faces, case.tau, case.cs, store, case.rho_b, **kw)
+    d.set_inflow_profile(f32(case.speed), case.theta)
+    d.init_fields(f32(case.rho0), f32(case.u0))
+    return d
+
+
+@pytest.mark.parametrize("faces", FACE_SETS)
+@pytest.mark.parametrize("nsteps", [1, 4])
+@pytest.mark.parametrize("flux", [False, True])
+def test_small_lattices_zones_and_flux_balance_populations(faces, nsteps, flux):
+    case = synth.random_small_case(13, 9, 7, faces, seed=21, solid_fraction=0.12, margin=0)
+    sponge, buffer = (3, 0.4), (2, 0.3)
+    dom = _gpu(case, sponge=sponge, buffer=buffer, flux_balance=flux)
+    dom.step(nsteps)
+    g = dom.export_populations().cpu().numpy()
+    kind, ub = oracle_inputs(case)
+    ueq = None
+    if flux:
+        ueq, before, after, delta = zones.flux_balanced_ueq(kind, faces, ub)
+        b, a, sh = dom.flux_balance_info()
+        assert b == pytest.approx(before, abs=1e-6) and abs(a) < 1e-5 and sh == pytest.approx(delta, abs=1e-7)
+    F = orc.init(kind, ub, f64_of_f32(case.rho0), f64_of_f32(case.u0), ueq=ueq)
+    F = zones.run(F, nsteps, kind, faces, ub, case.tau, case.cs, sponge=sponge, buffer=buffer, ueq=ueq)
+    _, wo, _ = orc.lattice()
+    G = g[lib_to_oracle_order()] + wo[:, None, None, None]
+    diff = np.abs(G - F)[:, kind != orc.SOLID]
+    assert diff.max() <= 2e-6, diff.max()
+
+
+@pytest.mark.parametrize("store", ["f32", "f16s"])
+def test_cube_with_sponge_and_buffers_200_steps(store):
+    case = synth.cube_case()
+    sponge, buffer = (6, 0.2), (5, 0.1)
+    dom = _gpu(case, store, sponge=sponge, buffer=buffer)
+    dom.step(200)
+    _, u = dom.macroscopic()
+    u = u.cpu().numpy().astype(np.float64)
+    kind, ub = oracle_inputs(case)
+    F = orc.init(kind, ub, None, f64_of_f32(case.u0))
+    F = zones.run(F, 200, kind, case.faces, ub, case.tau, case.cs, sponge=sponge, buffer=buffer)
+    _, ur = orc.macros(F, kind, ub)
+    err = rel_l2(u, ur, kind == orc.FLUID)
+    print(f"cube + zones {store}: rel L2 u = {err:.2e}")
+    assert err <= TOL_U[store]
+
+
+def test_flux_balance_info_off_and_on():
+    case = synth.random_small_case(13, 9, 7, FACE_SETS[3], seed=22, solid_fraction=0.2, margin=0)
+    d0 = _gpu(case)
+    b0, a0, s0 = d0.flux_balance_info()
+    assert s0 == 0.0 and a0 == b0
+    d1 = _gpu(case, flux_balance=True)
+    b1, a1, s1 = d1.flux_balance_info()
+    assert b1 == b0 and abs(a1) < 1e-5 * max(1.0, abs(b1)) and s1 != 0.0
