@@ -186,6 +186,16 @@ lbm_status lbm_macroscopic(lbm_domain *d, float *rho, float *u);
  * in the direction order of lbm_direction_table; solid cells export 0.  DEVICE float[19 * N]. */
 lbm_status lbm_export_populations(lbm_domain *d, float *g);
 
+/* Resume from a saved state (checkpoint / restart): g is a DEVICE float[19 * N] in the format of
+ * lbm_export_populations (post-collision populations, shifted, library direction order; solid
+ * cells ignored), written into the domain's in-place layout in its storage kind (rounded to 16 bits
+ * for FP16S / BF16S) together with the outflow side buffers; the step counter becomes `step`, which
+ * must be even (a state exported after an odd step can be resumed one step later, or as an even
+ * count).  Asynchronous; g may be reused once the stream has passed the call.  Exporting after an
+ * even number of steps, importing into a domain with the same mask, faces and parameters, and
+ * stepping on reproduces the uninterrupted run bit for bit. */
+lbm_status lbm_import_populations(lbm_domain *d, const float *g, long long step);
+
 /* The library's direction order: c[3*i + a] (int) and w[i] (float), i = 0..18.  Returns 19. */
 int lbm_direction_table(int *c, float *w);
 

@@ -60,10 +60,14 @@ __global__ void __launch_bounds__(kBlock, MINB) k_batch_step(BatchTables t) {
         for (int k = threadIdx.x; k < (int)(sizeof(StepArgs) / sizeof(int)); k += kBlock) dst[k] = src[k];
     }
     __syncthreads();
+    // FP32: the member's own choice of cells per thread, as in its single-domain launch
+    const bool d32 = S == LBM_F32 && sa.g.N >= kDual32MinCells;
     if constexpr (NEIGHBOR) {
-        neighbor_block<S, false, false>(sa, s_bid, face_blocks_of(sa.nface));
+        if (d32) neighbor_block<S, false, false, true>(sa, s_bid, face_blocks_of(sa.nface));
+        else neighbor_block<S, false, false, false>(sa, s_bid, face_blocks_of(sa.nface));
     } else if constexpr (S == LBM_F32) {
-        local_block<S, false, false>(sa, s_bid);
+        if (d32) local_block<S, false, false, true>(sa, s_bid);
+        else local_block<S, false, false, false>(sa, s_bid);
     } else {
         if (sa.pack16) local_block<S, false, true>(sa, s_bid);
         else local_block<S, false, false>(sa, s_bid);
@@ -91,10 +95,14 @@ __global__ void __launch_bounds__(kBlock, MINB) k_batch_step_p(const __grid_cons
     }
     const StepArgs &a = p.args[p.member[lo]];
     const unsigned bid = blockIdx.x - p.start[lo];
+    // FP32: the member's own choice of cells per thread, as in its single-domain launch
+    const bool d32 = S == LBM_F32 && a.g.N >= kDual32MinCells;
     if constexpr (NEIGHBOR) {
-        neighbor_block<S, false, false>(a, bid, face_blocks_of(a.nface));
+        if (d32) neighbor_block<S, false, false, true>(a, bid, face_blocks_of(a.nface));
+        else neighbor_block<S, false, false, false>(a, bid, face_blocks_of(a.nface));
     } else if constexpr (S == LBM_F32) {
-        local_block<S, false, false>(a, bid);
+        if (d32) local_block<S, false, false, true>(a, bid);
+        else local_block<S, false, false, false>(a, bid);
     } else {
         if (a.pack16) local_block<S, false, true>(a, bid);
         else local_block<S, false, false>(a, bid);
@@ -103,7 +111,8 @@ __global__ void __launch_bounds__(kBlock, MINB) k_batch_step_p(const __grid_cons
 
 // blocks of a member's launch of this kind (the same as its single-domain launch)
 template <int S> unsigned member_blocks(const StepArgs &a, bool neighbor) {
-    return lattice_blocks<S>(a.g.N) + (neighbor ? face_blocks_of(a.nface) : 0u);
+    const unsigned lb = a.g.N >= kDual32MinCells ? lattice_blocks<S, true>(a.g.N) : lattice_blocks<S, false>(a.g.N);
+    return lb + (neighbor ? face_blocks_of(a.nface) : 0u);
 }
 unsigned member_blocks(int store, const StepArgs &a, bool neighbor) {
     switch (store) {

@@ -435,6 +435,17 @@ lbm_status lbm_init_fields(lbm_domain *d, const float *rho, const float *u) {
     return st;
 }
 
+lbm_status lbm_import_populations(lbm_domain *d, const float *g, long long step) {
+    if (!d) return LBM_EINVAL;
+    if (!g) return fail(d, LBM_EINVAL, "import: NULL pointer");
+    if (step < 0 || (step & 1)) return fail(d, LBM_EINVAL, "import: step must be even and >= 0");
+    d->stg.valid = false;   // synthetic inflow anchors are re-evaluated at the next step
+    const StepArgs a = args_of(d);
+    lbm_status st = cuda_check(d, launch_import(d->p.store, a, g, d->stream), "import kernel");
+    if (st == LBM_OK) d->t = step;
+    return st;
+}
+
 lbm_status lbm_diagnostics(lbm_domain *d, double *out) {
     if (!d || !out) return LBM_EINVAL;
     const StepArgs a = args_of(d);

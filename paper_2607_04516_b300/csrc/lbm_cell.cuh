@@ -108,6 +108,32 @@ LBM_HD void cell_init(const StepArgs &a, long long n, const float *__restrict__ 
     }
 }
 
+// ---------------------------------------------------------------- state import (resume)
+// Write the post-collision populations gin (shifted FP32, population-major, library direction
+// order, as lbm_export_populations gives them) into layout B, the layout of an even step count:
+// the same stores as cell_init (store-side bounce-back slots, outflow side buffers).
+template <int S>
+LBM_HD void cell_import(const StepArgs &a, long long n, const float *__restrict__ gin) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    const uint8_t fl = a.flags[n];
+    if (fl & F_SOLID) return;
+    T *f = (T *)a.f;
+    const long long N = a.g.N;
+    float g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = gin[(long long)i * N + n];
+    const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        f[((nb >> i) & 1u) ? (long long)i * N + n + a.off[i] : (long long)opp(i) * N + n] = Cd::enc(g[i]);
+    if (fl & F_ZG) {
+        int x, y, z;
+        cell_coords(a.g, n, x, y, z);
+        store_side<T>(a.g, a.side, x, y, z, g, [](float v) { return Cd::enc(v); });
+    }
+}
+
 // ---------------------------------------------------------------- local step: A -> B
 template <int S, bool FORCE>
 LBM_HD void cell_local(const StepArgs &a, int n) {
@@ -866,26 +892,30 @@ constexpr int kBlock = 256;
 #endif
 constexpr bool kDual16 = LBM_DUAL16 != 0;
 
-// FP32 storage, unforced steps: two cells per thread through collide2 (1), or one cell per thread
-// (0); chosen by measurement on B300
-#ifndef LBM_DUAL32
-#define LBM_DUAL32 0
+// FP32 storage: lattices of at least this many cells take two cells per thread through collide2
+// (FP32x2), smaller ones one cell per thread -- on B300 the two-cell kernels are 1.5-2% faster on
+// the 12.8M-cell city and 19% slower on a 0.79M-cell lattice, where halving the blocks leaves a
+// ragged last wave.  (Unforced steps; the general path runs its two cells one after the other.)
+#ifndef LBM_DUAL32_MIN_CELLS
+#define LBM_DUAL32_MIN_CELLS (1ll << 21)
 #endif
-constexpr bool kDual32 = LBM_DUAL32 != 0;
+constexpr long long kDual32MinCells = LBM_DUAL32_MIN_CELLS;
 
-// cells per thread of the lattice blocks: two (16-bit storage, and FP32 with kDual32), else one
-template <int S> __host__ __device__ constexpr int cells_per_thread() { return (S == LBM_F32 && !kDual32) ? 1 : 2; }
+// cells per thread of the lattice blocks: two for 16-bit storage; for FP32 two when D32, else one
+template <int S, bool D32 = false> __host__ __device__ constexpr int cells_per_thread() {
+    return (S == LBM_F32 && !D32) ? 1 : 2;
+}
 
 // lattice blocks of a launch over N cells
-template <int S> __host__ __device__ inline unsigned lattice_blocks(long long N) {
-    const long long cpt = cells_per_thread<S>();
+template <int S, bool D32 = false> __host__ __device__ inline unsigned lattice_blocks(long long N) {
+    const long long cpt = cells_per_thread<S, D32>();
     return (unsigned)(((N + cpt - 1) / cpt + kBlock - 1) / kBlock);
 }
 __host__ __device__ inline unsigned face_blocks_of(long long nface) { return (unsigned)((nface + kBlock - 1) / kBlock); }
 
-template <int S, bool FORCE, bool PACK>
+template <int S, bool FORCE, bool PACK, bool D32 = false>
 __device__ __forceinline__ void local_block(const StepArgs &a, unsigned bid) {
-    if constexpr (S == LBM_F32 && cells_per_thread<S>() == 2) {
+    if constexpr (S == LBM_F32 && cells_per_thread<S, D32>() == 2) {
         const int n0 = (int)(bid * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
         if (n0 >= a.g.N) return;
         if constexpr (!FORCE) {
@@ -894,7 +924,7 @@ __device__ __forceinline__ void local_block(const StepArgs &a, unsigned bid) {
             cell_local<S, true>(a, n0);
             if (n1 < a.g.N) cell_local<S, true>(a, n1);
         }
-    } else if constexpr (cells_per_thread<S>() == 1) {
+    } else if constexpr (cells_per_thread<S, D32>() == 1) {
         const int n = (int)(bid * kBlock + threadIdx.x);
         if (n >= a.g.N) return;
         cell_local<S, FORCE>(a, n);
@@ -910,10 +940,10 @@ __device__ __forceinline__ void local_block(const StepArgs &a, unsigned bid) {
     }
 }
 
-template <int S, bool FORCE, bool PACK>
+template <int S, bool FORCE, bool PACK, bool D32 = false>
 __device__ __forceinline__ void neighbor_block(const StepArgs &a, unsigned bid, unsigned face_blocks) {
     if (bid >= face_blocks) {
-        if constexpr (S == LBM_F32 && cells_per_thread<S>() == 2) {
+        if constexpr (S == LBM_F32 && cells_per_thread<S, D32>() == 2) {
             const int n0 = (int)((bid - face_blocks) * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
             if (n0 >= a.g.N) return;
             if constexpr (!FORCE) {
@@ -922,7 +952,7 @@ __device__ __forceinline__ void neighbor_block(const StepArgs &a, unsigned bid, 
                 cell_neighbor_interior<S, true>(a, n0);
                 if (n1 < a.g.N) cell_neighbor_interior<S, true>(a, n1);
             }
-        } else if constexpr (cells_per_thread<S>() == 1) {
+        } else if constexpr (cells_per_thread<S, D32>() == 1) {
             const int n = (int)((bid - face_blocks) * kBlock + threadIdx.x);
             if (n >= a.g.N) return;
             cell_neighbor_interior<S, FORCE>(a, n);

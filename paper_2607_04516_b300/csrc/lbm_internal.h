@@ -11,6 +11,7 @@ constexpr int kRedBlocks = 148 * 8;   // diagnostics pass-1 blocks (8 per SM on 
 
 cudaError_t launch_flags(const uint8_t *mask, uint8_t *flags, uint32_t *info, const Geo &G, cudaStream_t s);
 cudaError_t launch_init(int store, const StepArgs &a, const float *rho, const float *u, cudaStream_t s);
+cudaError_t launch_import(int store, const StepArgs &a, const float *g, cudaStream_t s);
 void launch_step(int store, bool neighbor, bool force, const StepArgs &a, cudaStream_t s);
 cudaError_t launch_macros(int store, const StepArgs &a, bool layoutA, float *rho, float *u,
                           cudaStream_t s);

@@ -34,6 +34,13 @@ __global__ void k_flags(const uint8_t *__restrict__ mask, uint8_t *__restrict__ 
 }
 
 template <int S>
+__global__ void k_import(StepArgs a, const float *__restrict__ g) {
+    const long long G_N = a.g.N;
+    LBM_CELL_INDEX();
+    cell_import<S>(a, n, g);
+}
+
+template <int S>
 __global__ void k_init(StepArgs a, const float *__restrict__ rho, const float *__restrict__ u) {
     const long long G_N = a.g.N;
     LBM_CELL_INDEX();
@@ -41,18 +48,18 @@ __global__ void k_init(StepArgs a, const float *__restrict__ rho, const float *_
 }
 
 // PACK (16-bit storage with N and nx even): adjacent cell pairs with 4-byte accesses
-template <int S, bool FORCE, bool PACK>
+template <int S, bool FORCE, bool PACK, bool D32>
 __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_LOCAL) k_step_local(StepArgs a) {
-    local_block<S, FORCE, PACK>(a, blockIdx.x);
+    local_block<S, FORCE, PACK, D32>(a, blockIdx.x);
 }
 
 // Blocks [0, face_blocks) update the face-layer cells (general boundary resolution, ALU heavy);
 // the remaining blocks cover the lattice and update its interior cells.  Face blocks go first so
 // that their arithmetic overlaps the memory traffic of the interior blocks, and no warp mixes the
 // two paths.
-template <int S, bool FORCE, bool PACK>
+template <int S, bool FORCE, bool PACK, bool D32>
 __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_NEIGHBOR) k_step_neighbor(StepArgs a, unsigned face_blocks) {
-    neighbor_block<S, FORCE, PACK>(a, blockIdx.x, face_blocks);
+    neighbor_block<S, FORCE, PACK, D32>(a, blockIdx.x, face_blocks);
 }
 
 // Face tables (once per domain, after the flags; without them, as on lattices too large for their
@@ -203,23 +210,41 @@ cudaError_t launch_init(int store, const StepArgs &a, const float *rho, const fl
     }
 }
 
-template <int S, bool FORCE, bool PACK>
+template <int S>
+static cudaError_t import_t(const StepArgs &a, const float *g, cudaStream_t s) {
+    k_import<S><<<blocks_for(a.g.N), kBlock, 0, s>>>(a, g);
+    return cudaGetLastError();
+}
+cudaError_t launch_import(int store, const StepArgs &a, const float *g, cudaStream_t s) {
+    switch (store) {
+        case LBM_F32: return import_t<LBM_F32>(a, g, s);
+        case LBM_F16S: return import_t<LBM_F16S>(a, g, s);
+        default: return import_t<LBM_BF16S>(a, g, s);
+    }
+}
+
+template <int S, bool FORCE, bool PACK, bool D32>
 static void step_p(bool neighbor, const StepArgs &a, cudaStream_t s) {
-    const long long cpt = cells_per_thread<S>();
-    const unsigned lb = blocks_for((a.g.N + cpt - 1) / cpt);
+    const unsigned lb = lattice_blocks<S, D32>(a.g.N);
     if (neighbor) {
         const unsigned fb = blocks_for(a.nface);
-        k_step_neighbor<S, FORCE, PACK><<<fb + lb, kBlock, 0, s>>>(a, fb);
+        k_step_neighbor<S, FORCE, PACK, D32><<<fb + lb, kBlock, 0, s>>>(a, fb);
     } else {
-        k_step_local<S, FORCE, PACK><<<lb, kBlock, 0, s>>>(a);
+        k_step_local<S, FORCE, PACK, D32><<<lb, kBlock, 0, s>>>(a);
     }
 }
 // 16-bit storage: the local step uses adjacent packed pairs when the lattice allows it, the
-// neighbour step the (n, n + 256) pairs (faster for its shifted accesses, measured on B300)
+// neighbour step the (n, n + 256) pairs (faster for its shifted accesses, measured on B300).
+// FP32 storage: two cells per thread on lattices of at least kDual32MinCells cells.
 template <int S, bool FORCE>
 static void step_t(bool neighbor, const StepArgs &a, cudaStream_t s) {
-    if (S != LBM_F32 && a.pack16 && !neighbor) step_p<S, FORCE, true>(neighbor, a, s);
-    else step_p<S, FORCE, false>(neighbor, a, s);
+    if constexpr (S == LBM_F32) {
+        if (a.g.N >= kDual32MinCells) step_p<S, FORCE, false, true>(neighbor, a, s);
+        else step_p<S, FORCE, false, false>(neighbor, a, s);
+    } else {
+        if (a.pack16 && !neighbor) step_p<S, FORCE, true, false>(neighbor, a, s);
+        else step_p<S, FORCE, false, false>(neighbor, a, s);
+    }
 }
 template <int S>
 static void step_s(bool neighbor, bool force, const StepArgs &a, cudaStream_t s) {

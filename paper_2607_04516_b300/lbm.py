@@ -66,6 +66,7 @@ SIGNATURES = {
     "lbm_sample_columns": (_I, [_P, _P, _I, _P, _I, _P]),
     "lbm_macroscopic": (_I, [_P, _P, _P]),
     "lbm_export_populations": (_I, [_P, _P]),
+    "lbm_import_populations": (_I, [_P, _P, _LL]),
     "lbm_direction_table": (_I, [_P, _P]),
     "lbm_diagnostics": (_I, [_P, _P]),
     "lbm_diagnostics_noalloc": (_I, [_P, _P]),
@@ -171,6 +172,10 @@ def lbm_coriolis_omega(lat_deg: float, dt_si: float):
 
 def lbm_workspace_bytes(nx: int, ny: int, nz: int, params: lbm_params) -> int:
     return load(False).lbm_workspace_bytes(nx, ny, nz, ctypes.byref(params))
+
+
+def lbm_import_populations(dom, g, step: int):
+    _check(load().lbm_import_populations(dom, _ptr(g), int(step)), dom)
 
 
 def lbm_direction_table():
@@ -382,6 +387,13 @@ class Domain:
         g = torch.empty((19,) + self.shape, dtype=torch.float32, device=self.device)
         lbm_export_populations(self.dom, g)
         return g
+
+    def import_populations(self, g, step: int):
+        """Resume from ``g`` (CUDA float32 (19, nz, ny, nx), as ``export_populations`` returns)."""
+        import torch
+        g = torch.as_tensor(g, dtype=torch.float32, device=self.device).contiguous()
+        lbm_import_populations(self.dom, g, step)
+        self._keep_import = g
 
     def sample_columns(self, ij, k, out=None):
         import torch
