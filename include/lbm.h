@@ -114,6 +114,17 @@ lbm_status lbm_coriolis_omega(double lat_deg, double dt_si, float *out);
  * HOST outputs, any may be NULL. */
 lbm_status lbm_flux_balance_info(const lbm_domain *d, double *before, double *after, double *shift);
 
+/* Lattice units of a physical setup by Mach scaling (Sec. 3 run parameters, App. D: velocities
+ * scale with dt/dx, viscosities with dt/dx^2):
+ *   dx_si     cell size [m], > 0
+ *   u_ref_si  reference wind speed [m/s], > 0
+ *   ma_lbm    lattice Mach number of the reference speed, u_lbm / c_s with c_s = 1/sqrt(3), > 0
+ *   nu_si     kinematic viscosity [m^2/s], >= 0
+ * out (HOST double[4]): out[0] = dt_si = ma_lbm c_s dx_si / u_ref_si [s]; out[1] = u_ref in
+ * lattice units = ma_lbm c_s; out[2] = nu_lbm = nu_si dt_si / dx_si^2; out[3] = tau = 3 nu_lbm + 1/2
+ * (Eq. D.5 with dt = dx = 1).  LBM_EINVAL on out-of-range arguments. */
+lbm_status lbm_lattice_units(double dx_si, double u_ref_si, double ma_lbm, double nu_si, double *out);
+
 /* Lateral face kinds for a wind direction theta (radians, 0 = +x, counter-clockwise): a lateral
  * face is INFLOW_EQ when the wind enters through it (u . n_in > 1e-6 |u|), OUTFLOW_ZG otherwise;
  * z- = NOSLIP, z+ = FREESLIP.  face must hold 6 ints. */

@@ -314,6 +314,21 @@ lbm_status lbm_coriolis_omega(double lat_deg, double dt_si, float *out) {
     return LBM_OK;
 }
 
+lbm_status lbm_lattice_units(double dx_si, double u_ref_si, double ma_lbm, double nu_si, double *out) {
+    if (!out || !(dx_si > 0.0) || !(u_ref_si > 0.0) || !(ma_lbm > 0.0) || !(nu_si >= 0.0) || !std::isfinite(dx_si) ||
+        !std::isfinite(u_ref_si) || !std::isfinite(ma_lbm) || !std::isfinite(nu_si))
+        return LBM_EINVAL;
+    const double cs = 1.0 / std::sqrt(3.0);
+    const double u_lbm = ma_lbm * cs;
+    const double dt = u_lbm * dx_si / u_ref_si;
+    const double nu_lbm = nu_si * dt / (dx_si * dx_si);
+    out[0] = dt;
+    out[1] = u_lbm;
+    out[2] = nu_lbm;
+    out[3] = 3.0 * nu_lbm + 0.5;
+    return LBM_OK;
+}
+
 lbm_status lbm_faces_for_direction(float theta, int *face) {
     if (!face || !std::isfinite(theta)) return LBM_EINVAL;
     const double c = std::cos((double)theta), s = std::sin((double)theta), eps = 1e-6;

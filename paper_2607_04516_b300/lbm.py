@@ -54,6 +54,7 @@ _PP = ctypes.POINTER(lbm_params)
 SIGNATURES = {
     "lbm_params_default": (_I, [_PP]),
     "lbm_faces_for_direction": (_I, [_F, _P]),
+    "lbm_lattice_units": (_I, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _P]),
     "lbm_coriolis_omega": (_I, [ctypes.c_double, ctypes.c_double, _P]),
     "lbm_workspace_bytes": (_SZ, [_I, _I, _I, _PP]),
     "lbm_create_domain": (_I, [_P, _I, _I, _I, _PP, _P, _SZ, _P, ctypes.POINTER(_P)]),
@@ -162,6 +163,12 @@ def lbm_faces_for_direction(theta: float) -> tuple:
     face = (ctypes.c_int * 6)()
     _check(load(False).lbm_faces_for_direction(theta, face))
     return tuple(FACE_NAMES[v] for v in face)
+
+
+def lbm_lattice_units(dx_si: float, u_ref_si: float, ma_lbm: float, nu_si: float) -> dict:
+    out = (ctypes.c_double * 4)()
+    _check(load(False).lbm_lattice_units(float(dx_si), float(u_ref_si), float(ma_lbm), float(nu_si), out))
+    return {"dt_si": out[0], "u_lbm": out[1], "nu_lbm": out[2], "tau": out[3]}
 
 
 def lbm_coriolis_omega(lat_deg: float, dt_si: float):

@@ -193,3 +193,17 @@ def test_batch_workspace_bytes(lib):
     assert lbm.load(False).lbm_batch_workspace_bytes(5000) == 0
     small, big = lbm.load(False).lbm_batch_workspace_bytes(1), lbm.load(False).lbm_batch_workspace_bytes(40)
     assert 0 < small < big and big % 256 == 0
+
+
+def test_lattice_units_mach_scaling(lib):
+    """Mach scaling: u_lbm = u_si dt/dx = Ma c_s, nu_lbm = nu_si dt/dx^2, tau = 3 nu_lbm + 1/2."""
+    u = lbm.lbm_lattice_units(5.0, 5.3205, 0.10, 1.5e-5)
+    cs = 1.0 / math.sqrt(3.0)
+    assert u["u_lbm"] == pytest.approx(0.1 * cs, rel=1e-15)
+    assert 5.3205 * u["dt_si"] / 5.0 == pytest.approx(u["u_lbm"], rel=1e-14)
+    assert u["nu_lbm"] == pytest.approx(1.5e-5 * u["dt_si"] / 25.0, rel=1e-14)
+    assert u["tau"] == pytest.approx(3 * u["nu_lbm"] + 0.5, rel=1e-15)
+    for bad in [(0.0, 5.0, 0.1, 1e-5), (5.0, -1.0, 0.1, 1e-5), (5.0, 5.0, 0.0, 1e-5), (5.0, 5.0, 0.1, -1.0),
+                (float("nan"), 5.0, 0.1, 1e-5)]:
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_lattice_units(*bad)
