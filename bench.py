@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--store", default="f32", choices=list(STORE_BYTES))
     ap.add_argument("--workload", default="city400", choices=list(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10,zones,adjoint,ensemble",
+    ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10,zones,adjoint,ensemble,precision",
                     help="extra storage kinds timed after the main measurement ('' = none)")
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--adjoint-steps", type=int, default=2000,
@@ -367,6 +367,77 @@ def ensemble_leg(world: int, steps: int = 40):
     return out
 
 
+def precision_leg(world: int):
+    """Precision sweep: the same synthetic city (seed 1) at 256x256x64, 400x400x80 and
+    1000x1000x160 with populations stored as FP32, shifted FP16 and BF16 (FP32 arithmetic).  Per
+    size and 16-bit kind: GLUPS over 200 steps; relative L2 of u and of rho - 1 against the FP32
+    path after 200 steps (non-solid cells); relative error of the time-mean horizontal wind profile
+    (plane mean of |u_h| per height, every 10th state of steps 1..1000).  Plus the relative L2 of u
+    against the FP64 oracle on the 64x64x32 cube after 200 steps, per kind."""
+    import numpy as np
+    import torch
+    from paper_2607_04516_b300 import lbm, synth
+    out = {}
+    for (nx, ny, nz) in ((256, 256, 64), (400, 400, 80), (1000, 1000, 160)):
+        case = synth.city_case(nx=nx, ny=ny, nz=nz, seed=1)
+        fluid = torch.as_tensor(case.solid == 0, device="cuda")
+        res, prof = {}, {}
+        for store in ("f32", "f16s", "bf16s"):
+            d = lbm.Domain(case.solid, case.faces, case.tau, case.cs, store)
+            d.set_inflow_profile(case.speed.astype(np.float32), case.theta)
+            d.init_fields(None, case.u0.astype(np.float32))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(d.stream)
+            d.step(200)
+            e1.record(d.stream)
+            rho, u = d.macroscopic()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            res[store] = (rho, u, case.solid.size * 200 / (ms / 1e3) / 1e9)
+            acc = torch.zeros(nz, dtype=torch.float64, device="cuda")
+            for k in range(80):           # states 210 .. 1000, every 10th
+                d.step(10)
+                _, uu = d.macroscopic()
+                sp = torch.sqrt(uu[..., 0].double() ** 2 + uu[..., 1].double() ** 2)
+                acc += (sp * fluid).sum(dim=(1, 2)) / fluid.sum(dim=(1, 2)).clamp(min=1)
+            prof[store] = acc / 80
+            del d
+            torch.cuda.empty_cache()
+        r32, u32, g32 = res["f32"]
+        row = {"cells": nx * ny * nz, "f32_glups": g32}
+        for store in ("f16s", "bf16s"):
+            r, u, g = res[store]
+            du = torch.linalg.vector_norm((u - u32)[fluid].double()) / torch.linalg.vector_norm(u32[fluid].double())
+            dr = torch.linalg.vector_norm((r - r32)[fluid].double()) / torch.linalg.vector_norm((r32 - 1)[fluid].double())
+            dp = torch.linalg.vector_norm(prof[store] - prof["f32"]) / torch.linalg.vector_norm(prof["f32"])
+            row[store] = {"glups": g, "vs_f32": g / g32, "u_rel_l2_vs_f32_200": float(du),
+                          "rho_rel_l2_vs_f32_200": float(dr), "profile_rel_vs_f32_1000": float(dp)}
+        out[f"{nx}x{ny}x{nz}"] = row
+        del res
+        torch.cuda.empty_cache()
+    # against the FP64 oracle, 64x64x32 cube, 200 steps
+    from oracle import oracle as orc
+    cube = synth.cube_case()
+    kind = orc.classify(cube.solid, cube.faces)
+    ub = orc.expand_profile(cube.speed.astype(np.float32).astype(np.float64), cube.shape[0], 0.0)
+    F = orc.init(kind, ub, None, cube.u0.astype(np.float32).astype(np.float64))
+    F = orc.run(F, 200, kind, cube.faces, ub, cube.tau, cube.cs)
+    _, ur = orc.macros(F, kind, ub)
+    fl = kind == orc.FLUID
+    vs64 = {}
+    for store in ("f32", "f16s", "bf16s"):
+        d = lbm.Domain(cube.solid, cube.faces, cube.tau, cube.cs, store)
+        d.set_inflow_profile(cube.speed.astype(np.float32), cube.theta)
+        d.init_fields(None, cube.u0.astype(np.float32))
+        d.step(200)
+        _, u = d.macroscopic()
+        u = u.cpu().numpy().astype(np.float64)
+        vs64[store] = float(np.linalg.norm((u - ur)[fl]) / np.linalg.norm(ur[fl]))
+    out["cube64x64x32_u_rel_l2_vs_fp64_200"] = vs64
+    return out
+
+
 def cpu_baseline(case, seconds: float):
     """The FP64 oracle as it stands, on all host cores, over whole-lattice steps of this workload."""
     import numpy as np
@@ -450,6 +521,9 @@ def run_ours(args, rank, world):
             continue
         if st == "ensemble":
             variants[st] = ensemble_leg(world)
+            continue
+        if st == "precision":
+            variants[st] = precision_leg(world)
             continue
         if st == "zones":
             # FP32 with the boundary relaxation zones (Sec. 3): a top sponge 10 cells deep (rate 0.05
