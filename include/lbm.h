@@ -159,7 +159,9 @@ lbm_status lbm_set_stream(lbm_domain *d, void *stream);
  * L divides nz: level l covers the cells z in [l nz/L, (l+1) nz/L).  Otherwise s(z) is linear in
  * height between level centres (cell z sits at height z + 1/2, level l is centred at
  * (l + 1/2) nz / L) and constant beyond the outermost centres.  The host array may be reused as
- * soon as the call returns.  (The paper's per-cell boundary field comes from Kriging of lidar
+ * soon as the call returns.  The upload is asynchronous through a small ring of pinned host
+ * slots; the call waits only when the slot it reuses still has a copy in flight, four profile
+ * updates back.  (The paper's per-cell boundary field comes from Kriging of lidar
  * profiles, Sec. 3 and App. A; this entry point takes the per-height profile directly.) */
 lbm_status lbm_set_inflow_profile(lbm_domain *d, const float *speed, int L, float theta);
 

@@ -117,7 +117,20 @@ struct lbm_domain {
     std::vector<uint8_t> face_solid[6];   // solid mask on each face plane (n1 fastest)
     StgState stg;                // synthetic inflow turbulence (App. F)
     double flux_before, flux_after, flux_shift;   // flux balancing of the current profile
+    bool flux_valid;             // the three above describe the current profile
+    // pinned host staging of profile uploads (a ring, so that an upload never waits for the GPU);
+    // null if pinned host memory was not available (then pageable copies)
+    static constexpr int kStage = 4;
+    float *ub_pinned = nullptr;
+    cudaEvent_t ub_done[kStage];
+    int ub_slot;
     char err[512];
+    ~lbm_domain() {
+        if (ub_pinned) {
+            for (int k = 0; k < kStage; ++k) cudaEventDestroy(ub_done[k]);
+            cudaFreeHost(ub_pinned);
+        }
+    }
 };
 
 namespace {
@@ -375,6 +388,24 @@ lbm_status lbm_create_domain(const uint8_t *solid, int nx, int ny, int nz, const
     d->err[0] = 0;
     d->ub_host.assign((size_t)nz * 3, 0.0f);
     d->flux_before = d->flux_after = d->flux_shift = 0.0;
+    d->flux_valid = true;
+    d->ub_slot = 0;
+    d->ub_pinned = nullptr;
+    {
+        float *pin = nullptr;
+        if (cudaHostAlloc((void **)&pin, (size_t)lbm_domain::kStage * nz * 3 * sizeof(float), cudaHostAllocDefault) == cudaSuccess) {
+            int k = 0;
+            for (; k < lbm_domain::kStage; ++k)
+                if (cudaEventCreateWithFlags(&d->ub_done[k], cudaEventDisableTiming) != cudaSuccess) break;
+            if (k == lbm_domain::kStage) {
+                d->ub_pinned = pin;
+            } else {
+                for (int j = 0; j < k; ++j) cudaEventDestroy(d->ub_done[j]);
+                cudaFreeHost(pin);
+            }
+        }
+        cudaGetLastError();   // a failed pinned allocation only means pageable uploads
+    }
     for (int k = 0; k < 6; ++k) {
         // face plane k: (y, z), (x, z) or (x, y), first index fastest
         const int a = k / 2, hi = k & 1;
@@ -434,9 +465,28 @@ lbm_status lbm_set_inflow_profile(lbm_domain *d, const float *speed, int L, floa
         d->ub_host[3 * k + 1] = (float)(v * s);
         d->ub_host[3 * k + 2] = 0.0f;
     }
-    lbm_status st = cuda_check(d, cudaMemcpyAsync(d->ws + d->L.ub, d->ub_host.data(), (size_t)nz * 3 * sizeof(float),
-                                                  cudaMemcpyHostToDevice, d->stream), "profile upload");
-    flux_balance_update(d);
+    const size_t ub_bytes = (size_t)nz * 3 * sizeof(float);
+    lbm_status st;
+    if (d->ub_pinned) {
+        const int k = d->ub_slot;
+        d->ub_slot = (k + 1) % lbm_domain::kStage;
+        float *stage = d->ub_pinned + (size_t)k * nz * 3;
+        st = cuda_check(d, cudaEventSynchronize(d->ub_done[k]), "profile staging");   // its last copy ran
+        if (st == LBM_OK) {
+            std::memcpy(stage, d->ub_host.data(), ub_bytes);
+            st = cuda_check(d, cudaMemcpyAsync(d->ws + d->L.ub, stage, ub_bytes, cudaMemcpyHostToDevice, d->stream),
+                            "profile upload");
+        }
+        if (st == LBM_OK) st = cuda_check(d, cudaEventRecord(d->ub_done[k], d->stream), "profile staging");
+    } else {
+        st = cuda_check(d, cudaMemcpyAsync(d->ws + d->L.ub, d->ub_host.data(), ub_bytes, cudaMemcpyHostToDevice,
+                                           d->stream), "profile upload");
+    }
+    d->flux_valid = false;
+    if (d->p.flux_balance) {   // the shift is part of the step; otherwise computed on request
+        flux_balance_update(d);
+        d->flux_valid = true;
+    }
     if (st == LBM_OK && d->stg.on) st = stg_rebuild(d);
     return st;
 }
@@ -517,8 +567,13 @@ lbm_status lbm_step(lbm_domain *d, int n) {
 
 long long lbm_steps_done(const lbm_domain *d) { return d ? d->t : -1; }
 
-lbm_status lbm_flux_balance_info(const lbm_domain *d, double *before, double *after, double *shift) {
-    if (!d) return LBM_EINVAL;
+lbm_status lbm_flux_balance_info(const lbm_domain *d_, double *before, double *after, double *shift) {
+    if (!d_) return LBM_EINVAL;
+    lbm_domain *d = const_cast<lbm_domain *>(d_);   // lazily computed host-side bookkeeping
+    if (!d->flux_valid) {
+        flux_balance_update(d);
+        d->flux_valid = true;
+    }
     if (before) *before = d->flux_before;
     if (after) *after = d->flux_after;
     if (shift) *shift = d->p.flux_balance ? d->flux_shift : 0.0;
