@@ -616,6 +616,26 @@ LBM_HD void eq_lanes(const StepArgs &a, long long n0, long long n1, uint8_t f0, 
     }
 }
 
+// The same on packed words: the halves of equilibrium cells are replaced by their encoded
+// equilibrium.
+template <int S>
+LBM_HD void eq_lanes_packed(const StepArgs &a, long long n0, long long n1, uint8_t f0, uint8_t f1,
+                            uint32_t (&pk)[Q]) {
+    using Cd = Codec<S>;
+    constexpr int LS = Cd::kLog2;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!((c ? f1 : f0) & F_EQ)) continue;
+        float ge[Q];
+        eq_cell_g_s<LS>(a, c ? n1 : n0, ge);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const uint32_t b = Cd::template enc_bits_s<LS>(ge[i]);
+            pk[i] = c ? (pk[i] & 0xffffu) | (b << 16) : (pk[i] & 0xffff0000u) | b;
+        }
+    }
+}
+
 // pk: the pair's 19 words (input), f0 / f1: its flags
 template <int S>
 LBM_HD void cellp_local_dual_body(const StepArgs &a, int n0, uint32_t (&pk)[Q], uint8_t f0, uint8_t f1) {
@@ -624,26 +644,21 @@ LBM_HD void cellp_local_dual_body(const StepArgs &a, int n0, uint32_t (&pk)[Q], 
     constexpr int LS = Cd::kLog2;
     const int m = n0 >> 1;
     if ((f0 & f1) & F_SOLID) return;
-    float2 g[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = Cd::template dec2<LS>(pk[i]);
-    collide2<LS>(g, a);
-    if ((f0 | f1) & F_EQ) eq_lanes<LS>(a, n0, n0 + 1, f0, f1, g);
+    collide2_packed<S>(pk, a);
+    if ((f0 | f1) & F_EQ) eq_lanes_packed<S>(a, n0, n0 + 1, f0, f1, pk);
     if ((f0 | f1) & F_ZG) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const uint8_t fl = c ? f1 : f0;
             if (!(fl & F_ZG) || (fl & F_SOLID)) continue;
-            float gc[Q];
+            float gc[Q];   // the encoded values decode exactly, so the side copies keep their bits
 #pragma unroll
-            for (int i = 0; i < Q; ++i) gc[i] = c ? g[i].y : g[i].x;
+            for (int i = 0; i < Q; ++i) gc[i] = Cd::template dec_bits_s<LS>(c ? pk[i] >> 16 : pk[i] & 0xffffu);
             int x, y, z;
             cell_coords(a.g, n0 + c, x, y, z);
             store_side<T>(a.g, a.side, x, y, z, gc, [](float v) { return Cd::template enc_s<LS>(v); });
         }
     }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) pk[i] = Cd::template enc2<LS>(g[i]);
     // one 4-byte store per plane, unless a cell of the pair is solid (its slots may be receiving a
     // neighbour's bounce-back store) or redirects links
     if (!((f0 | f1) & (F_SOLID | F_REDIR))) {
@@ -675,12 +690,7 @@ LBM_HD void cell2_neighbor_interior_dual_body(const StepArgs &a, int n0, int n1,
     unsigned short *const *P = (unsigned short *const *)a.plane;
     const bool l0 = !(f0 & (F_SOLID | F_FACE)), l1 = !(f1 & (F_SOLID | F_FACE));
     if (!l0 && !l1) return;
-    float2 g[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = Cd::template dec2<LS>(pk[i]);
-    collide2<LS>(g, a);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) pk[i] = Cd::template enc2<LS>(g[i]);
+    collide2_packed<S>(pk, a);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         if (!(c ? l1 : l0)) continue;

@@ -427,6 +427,112 @@ LBM_HD float2 fma2(float2 a, float2 b, float2 c) {
 LBM_HD float2 sub2(float2 a, float2 b) { return fma2(b, v2(-1.0f), a); }   // a - b, exact rounding
 LBM_HD float2 fms2(float2 a, float2 b, float2 c) { return fma2(make_float2(-a.x, -a.y), b, c); }   // c - a b
 
+// The two-cell collision in two phases over an accessor get(i) -> float2 (the shifted populations
+// of direction i, scaled by 2^LOG2S) and put(i, float2), for callers short of registers: the
+// moments are accumulated pair by pair (s = g_i + g_i+1, d = g_i - g_i+1 of each opposite pair),
+// so that besides the populations only the ten running moments are live; the relaxation then
+// visits each direction once more.
+struct Relax2 {
+    float2 om, ux, uy, uz, e0, e1, q1, a1, e2, q2, a2;
+};
+
+template <int LOG2S, class Get>
+LBM_HD Relax2 collide2_moments(Get get, const StepArgs &a) {
+    constexpr float S = (float)(1 << LOG2S), iS = 1.0f / S;
+    float2 m0 = get(0), jx, jy, jz, sxx, syy, szz, sxy, sxz, syz;
+    {
+        const float2 u = get(1), w = get(2), s_ = add2(u, w), d_ = sub2(u, w);
+        m0 = add2(m0, s_); jx = d_; sxx = s_;
+    }
+    {
+        const float2 u = get(3), w = get(4), s_ = add2(u, w), d_ = sub2(u, w);
+        m0 = add2(m0, s_); jy = d_; syy = s_;
+    }
+    {
+        const float2 u = get(5), w = get(6), s_ = add2(u, w), d_ = sub2(u, w);
+        m0 = add2(m0, s_); jz = d_; szz = s_;
+    }
+    {   // (+x, +y)
+        const float2 u = get(7), w = get(8), s_ = add2(u, w), d_ = sub2(u, w);
+        m0 = add2(m0, s_); jx = add2(jx, d_); jy = add2(jy, d_); sxx = add2(sxx, s_); syy = add2(syy, s_); sxy = s_;
+    }
+    {   // (+x, +z)
+        const float2 u = get(9), w = get(10), s_ = add2(u, w), d_ = sub2(u, w);
+        m0 = add2(m0, s_); jx = add2(jx, d_); jz = add2(jz, d_); sxx = add2(sxx, s_); szz = add2(szz, s_); sxz = s_;
+    }
+    {   // (+y, +z)
+        const float2 u = get(11), w = get(12), s_ = add2(u, w), d_ = sub2(u, w);
+        m0 = add2(m0, s_); jy = add2(jy, d_); jz = add2(jz, d_); syy = add2(syy, s_); szz = add2(szz, s_); syz = s_;
+    }
+    {   // (+x, -y)
+        const float2 u = get(13), w = get(14), s_ = add2(u, w), d_ = sub2(u, w);
+        m0 = add2(m0, s_); jx = add2(jx, d_); jy = sub2(jy, d_); sxx = add2(sxx, s_); syy = add2(syy, s_); sxy = sub2(sxy, s_);
+    }
+    {   // (+x, -z)
+        const float2 u = get(15), w = get(16), s_ = add2(u, w), d_ = sub2(u, w);
+        m0 = add2(m0, s_); jx = add2(jx, d_); jz = sub2(jz, d_); sxx = add2(sxx, s_); szz = add2(szz, s_); sxz = sub2(sxz, s_);
+    }
+    {   // (+y, -z)
+        const float2 u = get(17), w = get(18), s_ = add2(u, w), d_ = sub2(u, w);
+        m0 = add2(m0, s_); jy = add2(jy, d_); jz = sub2(jz, d_); syy = add2(syy, s_); szz = add2(szz, s_); syz = sub2(syz, s_);
+    }
+    const float2 is = v2(iS);
+    const float2 drho = mul2(is, m0);
+    jx = mul2(is, jx); jy = mul2(is, jy); jz = mul2(is, jz);
+    sxx = mul2(is, sxx); syy = mul2(is, syy); szz = mul2(is, szz);
+    sxy = mul2(is, sxy); sxz = mul2(is, sxz); syz = mul2(is, syz);
+    const float2 rho = add2(v2(1.0f), drho);
+    Relax2 r;
+    // IEEE division and square roots here (measured faster than the special-function forms when
+    // both lanes go through them together)
+    const float2 irho = make_float2(1.0f / rho.x, 1.0f / rho.y);
+    r.ux = mul2(jx, irho); r.uy = mul2(jy, irho); r.uz = mul2(jz, irho);
+    const float2 d3r = mul2(drho, v2(1.0f / 3.0f));
+    const float2 pxx = fms2(jx, r.ux, sub2(sxx, d3r)), pyy = fms2(jy, r.uy, sub2(syy, d3r)),
+                 pzz = fms2(jz, r.uz, sub2(szz, d3r));
+    const float2 pxy = fms2(jx, r.uy, sxy), pxz = fms2(jx, r.uz, sxz), pyz = fms2(jy, r.uz, syz);
+    const float2 pd = fma2(pzz, pzz, fma2(pyy, pyy, mul2(pxx, pxx)));
+    const float2 po = fma2(pyz, pyz, fma2(pxz, pxz, mul2(pxy, pxy)));
+    const float2 pp2 = fma2(v2(4.0f), po, mul2(v2(2.0f), pd));   // 2 Pi:Pi
+    const float2 arg = fma2(mul2(v2(a.c2x18), irho), make_float2(sqrtf(pp2.x), sqrtf(pp2.y)), v2(a.tau * a.tau));
+    r.om = make_float2(2.0f / (a.tau + sqrtf(arg.x)), 2.0f / (a.tau + sqrtf(arg.y)));
+    const float2 uu = fma2(r.uz, r.uz, fma2(r.uy, r.uy, mul2(r.ux, r.ux)));
+    const float2 e = fms2(mul2(v2(1.5f), rho), uu, drho);
+    r.e0 = mul2(v2(S / 3.0f), e);
+    r.e1 = mul2(v2(S / 18.0f), e); r.q1 = mul2(v2(0.25f * S), rho); r.a1 = mul2(v2(S / 6.0f), rho);
+    r.e2 = mul2(v2(S / 36.0f), e); r.q2 = mul2(v2(0.125f * S), rho); r.a2 = mul2(v2(S / 12.0f), rho);
+    return r;
+}
+
+template <class Get, class Put>
+LBM_HD void collide2_relax(const Relax2 &r, Get get, Put put) {
+    {
+        const float2 g0 = get(0);
+        put(0, fma2(r.om, sub2(r.e0, g0), g0));
+    }
+#define LBM_PAIR2(I, CU, E, Qc, Ac)                                  \
+    {                                                               \
+        const float2 cu_ = (CU);                                    \
+        const float2 sym_ = fma2(mul2(Qc, cu_), cu_, E);            \
+        const float2 asym_ = mul2(Ac, cu_);                         \
+        const float2 gi_ = get(I), gj_ = get(I + 1);                \
+        put(I, fma2(r.om, sub2(add2(sym_, asym_), gi_), gi_));      \
+        put(I + 1, fma2(r.om, sub2(sub2(sym_, asym_), gj_), gj_));  \
+    }
+    LBM_PAIR2(1, r.ux, r.e1, r.q1, r.a1)
+    LBM_PAIR2(3, r.uy, r.e1, r.q1, r.a1)
+    LBM_PAIR2(5, r.uz, r.e1, r.q1, r.a1)
+    LBM_PAIR2(7, add2(r.ux, r.uy), r.e2, r.q2, r.a2)
+    LBM_PAIR2(9, add2(r.ux, r.uz), r.e2, r.q2, r.a2)
+    LBM_PAIR2(11, add2(r.uy, r.uz), r.e2, r.q2, r.a2)
+    LBM_PAIR2(13, sub2(r.ux, r.uy), r.e2, r.q2, r.a2)
+    LBM_PAIR2(15, sub2(r.ux, r.uz), r.e2, r.q2, r.a2)
+    LBM_PAIR2(17, sub2(r.uy, r.uz), r.e2, r.q2, r.a2)
+#undef LBM_PAIR2
+}
+
+// Two cells held as float pairs (FP32 storage): the moments as one balanced sum tree (more
+// independent instructions in flight than the pair-by-pair accumulation, measured faster there).
 template <int LOG2S>
 LBM_HD void collide2(float2 (&g)[Q], const StepArgs &a) {
     constexpr float S = (float)(1 << LOG2S), iS = 1.0f / S;
@@ -487,6 +593,24 @@ LBM_HD void collide2(float2 (&g)[Q], const StepArgs &a) {
     LBM_PAIR2(15, sub2(ux, uz), e2, q2, a2)
     LBM_PAIR2(17, sub2(uy, uz), e2, q2, a2)
 #undef LBM_PAIR2
+}
+
+// Two 16-bit cells held as their 19 packed storage words (low half: first cell): each direction
+// is decoded where it is used, once for the moments and once for the relaxation, and the result
+// is encoded in place, so that 19 registers instead of 38 carry the populations through the
+// collision.  The empty asm statements between the phases keep the compiler from holding the
+// first phase's decoded values live in place of the second decode.
+template <int S>
+LBM_HD void collide2_packed(uint32_t (&pk)[Q], const StepArgs &a) {
+    using Cd = Codec<S>;
+    constexpr int LS = Cd::kLog2;
+    const Relax2 r = collide2_moments<LS>([&](int i) { return Cd::template dec2<LS>(pk[i]); }, a);
+#ifdef __CUDA_ARCH__
+#pragma unroll
+    for (int i = 0; i < Q; ++i) asm volatile("" : "+r"(pk[i]));
+#endif
+    collide2_relax(r, [&](int i) { return Cd::template dec2<LS>(pk[i]); },
+                   [&](int i, float2 v) { pk[i] = Cd::template enc2<LS>(v); });
 }
 
 // ---------------------------------------------------------------- boundary resolution

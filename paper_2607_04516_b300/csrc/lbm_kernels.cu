@@ -56,10 +56,18 @@ __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_LOCAL) k_step_local(Ste
 // Blocks [0, face_blocks) update the face-layer cells (general boundary resolution, ALU heavy);
 // the remaining blocks cover the lattice and update its interior cells.  Face blocks go first so
 // that their arithmetic overlaps the memory traffic of the interior blocks, and no warp mixes the
-// two paths.
+// two paths.  The grid has one block per unit (units == gridDim.x); the 16-bit kernels are
+// written as a loop over units all the same: on B300 that form of the code runs the 16-bit
+// neighbour step 3-5% faster (0.310 against 0.326 ms on the 400 x 400 x 80 city) and the FP32 one
+// 5% slower, so FP32 keeps the plain form.
 template <int S, bool FORCE, bool PACK, bool D32>
-__global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_NEIGHBOR) k_step_neighbor(StepArgs a, unsigned face_blocks) {
-    neighbor_block<S, FORCE, PACK, D32>(a, blockIdx.x, face_blocks);
+__global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_NEIGHBOR) k_step_neighbor(StepArgs a, unsigned face_blocks,
+                                                                                 unsigned units) {
+    if constexpr (S == LBM_F32) {
+        neighbor_block<S, FORCE, PACK, D32>(a, blockIdx.x, face_blocks);
+    } else {
+        for (unsigned b = blockIdx.x; b < units; b += gridDim.x) neighbor_block<S, FORCE, PACK, D32>(a, b, face_blocks);
+    }
 }
 
 // Face tables (once per domain, after the flags; without them, as on lattices too large for their
@@ -228,7 +236,7 @@ static void step_p(bool neighbor, const StepArgs &a, cudaStream_t s) {
     const unsigned lb = lattice_blocks<S, D32>(a.g.N);
     if (neighbor) {
         const unsigned fb = blocks_for(a.nface);
-        k_step_neighbor<S, FORCE, PACK, D32><<<fb + lb, kBlock, 0, s>>>(a, fb);
+        k_step_neighbor<S, FORCE, PACK, D32><<<fb + lb, kBlock, 0, s>>>(a, fb, fb + lb);
     } else {
         k_step_local<S, FORCE, PACK, D32><<<lb, kBlock, 0, s>>>(a);
     }
