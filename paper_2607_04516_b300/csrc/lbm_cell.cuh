@@ -306,6 +306,9 @@ LBM_HD void cell_neighbor_face(const StepArgs &a, uint8_t fl, int x, int y, int 
 //   tab[(1 + i) ngen + t]          gather element of direction i (fluid cells)
 //   tab[(20 + j) ngen + t]         first scatter element of direction j (kFtNone: none)
 //   tab[(39 + j) ngen + t]         second scatter element (kFtNone: none)
+//   tab[58 ngen + t]               bit j: direction j scatters to its plain target alone (element
+//                                  j N + n + c_j), so its two scatter words need not be read
+//   tab[59 ngen + t]               bit j: direction j has a second scatter element
 
 template <int S>
 LBM_HD void cell_face_table(const StepArgs &a, int t, uint32_t *__restrict__ tab) {
@@ -337,6 +340,7 @@ LBM_HD void cell_face_table(const StepArgs &a, int t, uint32_t *__restrict__ tab
         tab[(1 + i) * ng + t] = gv;
     }
     const bool fluid = !(fl & F_EQ);
+    uint32_t plain = 0, second = 0;
     for (int j = 0; j < Q; ++j) {
         uint32_t v[2] = {kFtNone, kFtNone};
         int cnt = 0;
@@ -348,7 +352,11 @@ LBM_HD void cell_face_table(const StepArgs &a, int t, uint32_t *__restrict__ tab
         if (cnt > 2) head |= kFtGeneral;
         tab[(1 + Q + j) * ng + t] = v[0];
         tab[(1 + 2 * Q + j) * ng + t] = v[1];
+        if (cnt == 1 && v[0] == code(0, (long long)j * a.g.N + n + a.off[j])) plain |= 1u << j;
+        if (cnt >= 2) second |= 1u << j;
     }
+    tab[(1 + 3 * Q) * ng + t] = plain;
+    tab[(2 + 3 * Q) * ng + t] = second;
     tab[t] = (fl & F_SOLID) ? kFtNone : head;
 }
 
@@ -364,7 +372,7 @@ LBM_HD bool cell_neighbor_table(const StepArgs &a, int t) {
     const uint32_t *__restrict__ tab = a.ftab;
     const long long ng = a.ngen;
     uint32_t e[Q];
-    const uint32_t head = tab[t];
+    const uint32_t head = tab[t], plain = tab[(1 + 3 * Q) * ng + t], second = tab[(2 + 3 * Q) * ng + t];
 #pragma unroll
     for (int i = 0; i < Q; ++i) e[i] = tab[(1 + i) * ng + t];
     if (head == kFtNone) return true;   // solid
@@ -378,12 +386,18 @@ LBM_HD bool cell_neighbor_table(const StepArgs &a, int t) {
         collide<FORCE>(g, a);
         if (FORCE) nudge(a, (long long)(head & kFtCell), g);   // relaxation zones ride on the general (forced) path
     }
+    // plain directions store without reading their scatter words; the others read one or two
+    const long long n = (long long)(head & kFtCell);
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const T v = Cd::enc(g[j]);
-        const uint32_t e0 = tab[(1 + Q + j) * ng + t], e1 = tab[(1 + 2 * Q + j) * ng + t];
+        if ((plain >> j) & 1u) {
+            ((T *)a.plane[j])[n + a.off[j]] = v;
+            continue;
+        }
+        const uint32_t e0 = tab[(1 + Q + j) * ng + t];
         if (e0 != kFtNone) f[e0] = v;
-        if (e1 != kFtNone) f[e1] = v;
+        if ((second >> j) & 1u) f[tab[(1 + 2 * Q + j) * ng + t]] = v;
     }
     return true;
 }

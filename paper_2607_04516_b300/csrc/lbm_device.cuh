@@ -236,7 +236,7 @@ constexpr uint32_t kFtNone = 0xffffffffu;      // no element (head: a solid cell
 constexpr uint32_t kFtGeneral = 0x80000000u;   // head bit: the cell keeps the general resolution
 constexpr uint32_t kFtEq = 0x40000000u;        // head bit: an equilibrium cell
 constexpr uint32_t kFtCell = 0x3fffffffu;      // head bits of the cell index
-constexpr int kFtWords = 1 + 3 * Q;            // words per face cell
+constexpr int kFtWords = 3 + 3 * Q;            // words per face cell
 
 // The z face layers whose cells (with interior x and y) take the layer path: no-slip or free-slip
 // faces on a lattice at least 3 x 3 x 2.
