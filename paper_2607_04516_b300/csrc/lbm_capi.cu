@@ -190,6 +190,7 @@ StepArgs args_of(const lbm_domain *d) {
         for (int k = 0; k < 4; ++k)
             if (d->p.face[k] == LBM_FACE_INFLOW_EQ || d->p.face[k] == LBM_FACE_OUTFLOW_ZG) a.buffer_faces |= 1 << k;
     a.flux_balance = d->p.flux_balance;
+    set_divisors(a);
     a.flux_shift = d->p.flux_balance ? (float)d->flux_shift : 0.0f;
     if (d->stg.on && d->stg.valid) {
         const StgState &s = d->stg;

@@ -750,6 +750,18 @@ LBM_HD void cell2_neighbor_interior_dual(const StepArgs &a, int n0, int n1, bool
 // consecutive cells of a plane): both cells' loads are issued before either is computed, and both
 // go through one collide2 (FP32x2 instructions).  Stores per cell, as in the one-cell kernels.
 
+// Collision of the pair: unforced, or with the body force and the zone nudging (FORCE).
+template <bool FORCE>
+LBM_HD void collide2_f32(const StepArgs &a, int n0, int n1, float2 (&g)[Q]) {
+    if constexpr (FORCE) {
+        const float2 drho = collide2_forced<0>(g, a);
+        nudge2(a, n0, n1, drho, g);
+    } else {
+        collide2<0>(g, a);
+    }
+}
+
+template <bool FORCE = false>
 LBM_HD void cell2_local_dual_f32(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
     float *const *P = (float *const *)a.plane;
     float2 g[Q];   // loaded before the flags are known (n1 may be past N: guard region)
@@ -757,7 +769,7 @@ LBM_HD void cell2_local_dual_f32(const StepArgs &a, int n0, int n1, bool v0, boo
     for (int i = 0; i < Q; ++i) g[i] = make_float2(ld_early_f32(P[i] + n0), ld_early_f32(P[i] + n1));
     const uint8_t f0 = v0 ? a.flags[n0] : F_SOLID, f1 = v1 ? a.flags[n1] : F_SOLID;
     if ((f0 & f1) & F_SOLID) return;
-    collide2<0>(g, a);
+    collide2_f32<FORCE>(a, n0, n1, g);
     if ((f0 | f1) & F_EQ) eq_lanes<0>(a, n0, n1, f0, f1, g);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
@@ -786,6 +798,7 @@ LBM_HD void cell2_local_dual_f32(const StepArgs &a, int n0, int n1, bool v0, boo
     }
 }
 
+template <bool FORCE = false>
 LBM_HD void cell2_neighbor_interior_dual_f32(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
     float *const *P = (float *const *)a.plane;
     float2 g[Q];   // loaded before the flags are known (guard region after the planes)
@@ -797,7 +810,7 @@ LBM_HD void cell2_neighbor_interior_dual_f32(const StepArgs &a, int n0, int n1, 
     const uint8_t f0 = v0 ? a.flags[n0] : F_SOLID, f1 = v1 ? a.flags[n1] : F_SOLID;
     const bool l0 = !(f0 & (F_SOLID | F_FACE)), l1 = !(f1 & (F_SOLID | F_FACE));
     if (!l0 && !l1) return;
-    collide2<0>(g, a);
+    collide2_f32<FORCE>(a, n0, n1, g);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         if (!(c ? l1 : l0)) continue;
@@ -942,12 +955,7 @@ __device__ __forceinline__ void local_block(const StepArgs &a, unsigned bid) {
     if constexpr (S == LBM_F32 && cells_per_thread<S, D32>() == 2) {
         const int n0 = (int)(bid * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
         if (n0 >= a.g.N) return;
-        if constexpr (!FORCE) {
-            cell2_local_dual_f32(a, n0, n1, true, n1 < a.g.N);
-        } else {
-            cell_local<S, true>(a, n0);
-            if (n1 < a.g.N) cell_local<S, true>(a, n1);
-        }
+        cell2_local_dual_f32<FORCE>(a, n0, n1, true, n1 < a.g.N);
     } else if constexpr (cells_per_thread<S, D32>() == 1) {
         const int n = (int)(bid * kBlock + threadIdx.x);
         if (n >= a.g.N) return;
@@ -970,12 +978,7 @@ __device__ __forceinline__ void neighbor_block(const StepArgs &a, unsigned bid, 
         if constexpr (S == LBM_F32 && cells_per_thread<S, D32>() == 2) {
             const int n0 = (int)((bid - face_blocks) * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
             if (n0 >= a.g.N) return;
-            if constexpr (!FORCE) {
-                cell2_neighbor_interior_dual_f32(a, n0, n1, true, n1 < a.g.N);
-            } else {
-                cell_neighbor_interior<S, true>(a, n0);
-                if (n1 < a.g.N) cell_neighbor_interior<S, true>(a, n1);
-            }
+            cell2_neighbor_interior_dual_f32<FORCE>(a, n0, n1, true, n1 < a.g.N);
         } else if constexpr (cells_per_thread<S, D32>() == 1) {
             const int n = (int)((bid - face_blocks) * kBlock + threadIdx.x);
             if (n >= a.g.N) return;

@@ -229,7 +229,24 @@ struct StepArgs {
     int buffer_faces;
     float flux_shift;           // flux balancing: inward normal shift of equilibrium velocities
     int flux_balance;           // flux balancing on (the shift follows the profile)
+    uint32_t div_nx, div_ny;    // multipliers for exact division by nx, ny (see set_divisors)
+    int shr_nx, shr_ny;
 };
+
+// Division of a cell index 0 <= n < 2^31 by an invariant d >= 1 as floor(n m / 2^(31 + l)) with
+// l = ceil(log2 d) and m = ceil(2^(31 + l) / d) < 2^32: exact because m d - 2^(31 + l) < d <= 2^l
+// (Granlund and Montgomery, "Division by invariant integers using multiplication", 1994, Thm 4.2).
+inline void divisor_of(int d, uint32_t &m, int &shr) {
+    int l = 0;
+    while ((1ll << l) < d) ++l;
+    shr = 31 + l;
+    m = (uint32_t)((((unsigned long long)1 << shr) + (unsigned long long)d - 1) / (unsigned long long)d);
+}
+inline void set_divisors(StepArgs &a) {
+    divisor_of(a.g.nx, a.div_nx, a.shr_nx);
+    divisor_of(a.g.ny, a.div_ny, a.shr_ny);
+}
+LBM_HD int div_by(int n, uint32_t m, int shr) { return (int)(((unsigned long long)(unsigned)n * m) >> shr); }
 
 // Face tables (see cell_face_table): 32-bit storage-element codes per face cell
 constexpr uint32_t kFtNone = 0xffffffffu;      // no element (head: a solid cell)
@@ -595,6 +612,86 @@ LBM_HD void collide2(float2 (&g)[Q], const StepArgs &a) {
 #undef LBM_PAIR2
 }
 
+// Forced pair form of collide<true>: the body force F = f + 2 Omega x j of each lane (uniform part
+// plus Coriolis, App. E), the half-force velocity u = (j + F/2) / rho in the equilibrium and the
+// stress, and Guo's source (1 - om/2) w_i [3 (c_i - u).F + 9 (c_i.u)(c_i.F)] added to the relaxed
+// populations.  On an opposite pair (c_j = -c_i) the source splits like the equilibrium into a
+// shared even part (1 - om/2) w (9 (c.u)(c.F) - 3 u.F) and an odd part +-(1 - om/2) 3 w c.F.  The
+// same arithmetic per lane as the one-cell form up to the order of rounding.  Returns drho.
+template <int LOG2S>
+LBM_HD float2 collide2_forced(float2 (&g)[Q], const StepArgs &a) {
+    constexpr float S = (float)(1 << LOG2S), iS = 1.0f / S;
+    const float2 s1 = add2(g[1], g[2]), d1 = sub2(g[1], g[2]);
+    const float2 s3 = add2(g[3], g[4]), d3 = sub2(g[3], g[4]);
+    const float2 s5 = add2(g[5], g[6]), d5 = sub2(g[5], g[6]);
+    const float2 s7 = add2(g[7], g[8]), d7 = sub2(g[7], g[8]);
+    const float2 s9 = add2(g[9], g[10]), d9 = sub2(g[9], g[10]);
+    const float2 s11 = add2(g[11], g[12]), d11 = sub2(g[11], g[12]);
+    const float2 s13 = add2(g[13], g[14]), d13 = sub2(g[13], g[14]);
+    const float2 s15 = add2(g[15], g[16]), d15 = sub2(g[15], g[16]);
+    const float2 s17 = add2(g[17], g[18]), d17 = sub2(g[17], g[18]);
+    const float2 is = v2(iS);
+    const float2 drho = mul2(is, add2(add2(add2(g[0], add2(add2(s1, s3), s5)), add2(add2(s7, s9), add2(s11, s13))),
+                                      add2(s15, s17)));
+    float2 jx = mul2(is, add2(add2(add2(add2(d1, d7), d9), d13), d15));
+    float2 jy = mul2(is, add2(sub2(add2(add2(d3, d7), d11), d13), d17));
+    float2 jz = mul2(is, sub2(sub2(add2(add2(d5, d9), d11), d15), d17));
+    const float2 sxx = mul2(is, add2(add2(add2(add2(s1, s7), s9), s13), s15));
+    const float2 syy = mul2(is, add2(add2(add2(add2(s3, s7), s11), s13), s17));
+    const float2 szz = mul2(is, add2(add2(add2(add2(s5, s9), s11), s15), s17));
+    const float2 sxy = mul2(is, sub2(s7, s13)), sxz = mul2(is, sub2(s9, s15)), syz = mul2(is, sub2(s11, s17));
+    const float2 rho = add2(v2(1.0f), drho);
+    const float2 irho = make_float2(1.0f / rho.x, 1.0f / rho.y);
+    // F = f + 2 Omega x j
+    const float2 Fx = fma2(v2(2.0f), sub2(mul2(v2(a.oy), jz), mul2(v2(a.oz), jy)), v2(a.fx));
+    const float2 Fy = fma2(v2(2.0f), sub2(mul2(v2(a.oz), jx), mul2(v2(a.ox), jz)), v2(a.fy));
+    const float2 Fz = fma2(v2(2.0f), sub2(mul2(v2(a.ox), jy), mul2(v2(a.oy), jx)), v2(a.fz));
+    jx = fma2(v2(0.5f), Fx, jx);
+    jy = fma2(v2(0.5f), Fy, jy);
+    jz = fma2(v2(0.5f), Fz, jz);
+    const float2 ux = mul2(jx, irho), uy = mul2(jy, irho), uz = mul2(jz, irho);
+    const float2 d3r = mul2(drho, v2(1.0f / 3.0f));
+    const float2 pxx = fms2(jx, ux, sub2(sxx, d3r)), pyy = fms2(jy, uy, sub2(syy, d3r)),
+                 pzz = fms2(jz, uz, sub2(szz, d3r));
+    const float2 pxy = fms2(jx, uy, sxy), pxz = fms2(jx, uz, sxz), pyz = fms2(jy, uz, syz);
+    const float2 pd = fma2(pzz, pzz, fma2(pyy, pyy, mul2(pxx, pxx)));
+    const float2 po = fma2(pyz, pyz, fma2(pxz, pxz, mul2(pxy, pxy)));
+    const float2 pp2 = fma2(v2(4.0f), po, mul2(v2(2.0f), pd));   // 2 Pi:Pi
+    const float2 arg = fma2(mul2(v2(a.c2x18), irho), make_float2(sqrtf(pp2.x), sqrtf(pp2.y)), v2(a.tau * a.tau));
+    const float2 om = make_float2(2.0f / (a.tau + sqrtf(arg.x)), 2.0f / (a.tau + sqrtf(arg.y)));
+    const float2 uu = fma2(uz, uz, fma2(uy, uy, mul2(ux, ux)));
+    const float2 e = fms2(mul2(v2(1.5f), rho), uu, drho);
+    // source coefficients: pre = (1 - om/2) S, uf = u.F
+    const float2 pre = mul2(v2(S), fma2(v2(-0.5f), om, v2(1.0f)));
+    const float2 uf = fma2(uz, Fz, fma2(uy, Fy, mul2(ux, Fx)));
+    const float2 u3 = mul2(v2(-3.0f), uf);
+    g[0] = add2(fma2(om, sub2(mul2(v2(S / 3.0f), e), g[0]), g[0]), mul2(mul2(v2(1.0f / 3.0f), pre), u3));
+    const float2 e1 = mul2(v2(S / 18.0f), e), q1 = mul2(v2(0.25f * S), rho), a1 = mul2(v2(S / 6.0f), rho);
+    const float2 e2 = mul2(v2(S / 36.0f), e), q2 = mul2(v2(0.125f * S), rho), a2 = mul2(v2(S / 12.0f), rho);
+    const float2 p1 = mul2(v2(1.0f / 18.0f), pre), p2 = mul2(v2(1.0f / 36.0f), pre);
+#define LBM_PAIR2F(I, CU, CF, E, Qc, Ac, Pw)                                        \
+    {                                                                                \
+        const float2 cu_ = (CU), cf_ = (CF);                                         \
+        const float2 sym_ = fma2(mul2(Qc, cu_), cu_, E);                             \
+        const float2 asym_ = mul2(Ac, cu_);                                          \
+        const float2 fs_ = mul2(Pw, fma2(mul2(v2(9.0f), cu_), cf_, u3));             \
+        const float2 fa_ = mul2(mul2(v2(3.0f), Pw), cf_);                            \
+        g[I] = add2(fma2(om, sub2(add2(sym_, asym_), g[I]), g[I]), add2(fs_, fa_));  \
+        g[I + 1] = add2(fma2(om, sub2(sub2(sym_, asym_), g[I + 1]), g[I + 1]), sub2(fs_, fa_)); \
+    }
+    LBM_PAIR2F(1, ux, Fx, e1, q1, a1, p1)
+    LBM_PAIR2F(3, uy, Fy, e1, q1, a1, p1)
+    LBM_PAIR2F(5, uz, Fz, e1, q1, a1, p1)
+    LBM_PAIR2F(7, add2(ux, uy), add2(Fx, Fy), e2, q2, a2, p2)
+    LBM_PAIR2F(9, add2(ux, uz), add2(Fx, Fz), e2, q2, a2, p2)
+    LBM_PAIR2F(11, add2(uy, uz), add2(Fy, Fz), e2, q2, a2, p2)
+    LBM_PAIR2F(13, sub2(ux, uy), sub2(Fx, Fy), e2, q2, a2, p2)
+    LBM_PAIR2F(15, sub2(ux, uz), sub2(Fx, Fz), e2, q2, a2, p2)
+    LBM_PAIR2F(17, sub2(uy, uz), sub2(Fy, Fz), e2, q2, a2, p2)
+#undef LBM_PAIR2F
+    return drho;
+}
+
 // Two 16-bit cells held as their 19 packed storage words (low half: first cell): each direction
 // is decoded where it is used, once for the moments and once for the relaxation, and the result
 // is encoded in place, so that 19 registers instead of 38 carry the populations through the
@@ -919,10 +1016,7 @@ LBM_HD void eq_velocity(const StepArgs &a, long long n, float &ux, float &uy, fl
 // Relaxation zones next to the top and the open lateral faces (Sec. 3): after its collision the fluid
 // cell n relaxes toward f^eq(rho, u_b(z)) with the largest zone rate s = sigma ((w - d)/w)^2 over the
 // zones whose face layer is d < w cells away.  g: shifted post-collision populations (in/out).
-LBM_HD void nudge(const StepArgs &a, long long n, float (&g)[Q]) {
-    if (a.sponge_top <= 0 && a.buffer_faces == 0) return;
-    int x, y, z;
-    cell_coords(a.g, n, x, y, z);
+LBM_HD float zone_rate(const StepArgs &a, int x, int y, int z) {
     float s = 0.0f;
     if (a.sponge_top > 0) {
         const int d = a.g.nz - 1 - z;
@@ -940,6 +1034,14 @@ LBM_HD void nudge(const StepArgs &a, long long n, float (&g)[Q]) {
             s = fmaxf(s, a.buffer_sigma * r * r);
         }
     }
+    return s;
+}
+
+LBM_HD void nudge(const StepArgs &a, long long n, float (&g)[Q]) {
+    if (a.sponge_top <= 0 && a.buffer_faces == 0) return;
+    int x, y, z;
+    cell_coords(a.g, n, x, y, z);
+    const float s = zone_rate(a, x, y, z);
     if (s <= 0.0f) return;
     float drho = 0.0f;
 #pragma unroll
@@ -948,6 +1050,39 @@ LBM_HD void nudge(const StepArgs &a, long long n, float (&g)[Q]) {
     equilibrium_shifted(drho, a.ub[3 * z], a.ub[3 * z + 1], a.ub[3 * z + 2], geq);
 #pragma unroll
     for (int i = 0; i < Q; ++i) g[i] = fmaf(-s, g[i] - geq[i], g[i]);
+}
+
+// The nudging of two cells n0, n1 (lanes x, y of g; 32-bit cell indices, n1 possibly past the
+// lattice for a lane that is discarded), lane by lane as nudge(); a lane whose rate is 0 keeps its
+// values exactly.
+// drho: the pair's density deviation (the collision conserves it, so the pre-collision value
+// serves; equal to the sum of the relaxed populations up to rounding).
+LBM_HD void nudge2(const StepArgs &a, int n0, int n1, float2 drho, float2 (&g)[Q]) {
+    if (a.sponge_top <= 0 && a.buffer_faces == 0) return;
+    float s[2];
+    int zc[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int n = c ? n1 : n0;
+        const int r = div_by(n, a.div_nx, a.shr_nx), x = n - r * a.g.nx;
+        const int z = div_by(r, a.div_ny, a.shr_ny), y = r - z * a.g.ny;
+        zc[c] = z < a.g.nz ? z : a.g.nz - 1;
+        s[c] = zone_rate(a, x, y, zc[c]);
+    }
+    if (s[0] <= 0.0f && s[1] <= 0.0f) return;
+    const float2 ux = make_float2(a.ub[3 * zc[0]], a.ub[3 * zc[1]]);
+    const float2 uy = make_float2(a.ub[3 * zc[0] + 1], a.ub[3 * zc[1] + 1]);
+    const float2 uz = make_float2(a.ub[3 * zc[0] + 2], a.ub[3 * zc[1] + 2]);
+    const float2 rho = add2(v2(1.0f), drho);
+    const float2 ms = make_float2(-s[0], -s[1]);
+    // direction by direction (fewer live registers than the opposite-pair form, measured faster)
+    const float2 u2 = mul2(v2(1.5f), fma2(uz, uz, fma2(uy, uy, mul2(ux, ux))));
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float2 cu = fma2(v2((float)cz(i)), uz, fma2(v2((float)cy(i)), uy, mul2(v2((float)cx(i)), ux)));
+        const float2 geq = mul2(v2(wgt(i)), fma2(rho, sub2(mul2(cu, fma2(v2(4.5f), cu, v2(3.0f))), u2), drho));
+        g[i] = fma2(ms, sub2(g[i], geq), g[i]);
+    }
 }
 
 // Shifted equilibrium of an equilibrium cell.

@@ -48,8 +48,18 @@ __global__ void k_init(StepArgs a, const float *__restrict__ rho, const float *_
 }
 
 // PACK (16-bit storage with N and nx even): adjacent cell pairs with 4-byte accesses
+// resident blocks per SM of the forced FP32 step kernels: their pair collision with the body force
+// and the zone nudging spills heavily at 64 registers; at 80 (3 blocks) FP32 zones run 15% faster
+// on the 400 x 400 x 80 city, while the 16-bit forced kernels are faster at 4 blocks
+#ifndef LBM_MIN_BLOCKS_FORCED32
+#define LBM_MIN_BLOCKS_FORCED32 3
+#endif
+template <int S, bool FORCE> constexpr int min_blocks(int unforced) {
+    return (FORCE && S == LBM_F32) ? LBM_MIN_BLOCKS_FORCED32 : unforced;
+}
+
 template <int S, bool FORCE, bool PACK, bool D32>
-__global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_LOCAL) k_step_local(StepArgs a) {
+__global__ void __launch_bounds__(kBlock, min_blocks<S, FORCE>(LBM_MIN_BLOCKS_LOCAL)) k_step_local(StepArgs a) {
     local_block<S, FORCE, PACK, D32>(a, blockIdx.x);
 }
 
@@ -61,7 +71,7 @@ __global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_LOCAL) k_step_local(Ste
 // neighbour step 3-5% faster (0.310 against 0.326 ms on the 400 x 400 x 80 city) and the FP32 one
 // 5% slower, so FP32 keeps the plain form.
 template <int S, bool FORCE, bool PACK, bool D32>
-__global__ void __launch_bounds__(kBlock, LBM_MIN_BLOCKS_NEIGHBOR) k_step_neighbor(StepArgs a, unsigned face_blocks,
+__global__ void __launch_bounds__(kBlock, min_blocks<S, FORCE>(LBM_MIN_BLOCKS_NEIGHBOR)) k_step_neighbor(StepArgs a, unsigned face_blocks,
                                                                                  unsigned units) {
     if constexpr (S == LBM_F32) {
         neighbor_block<S, FORCE, PACK, D32>(a, blockIdx.x, face_blocks);

@@ -74,3 +74,29 @@ def test_flux_balance_info_off_and_on():
     d1 = _gpu(case, flux_balance=True)
     b1, a1, s1 = d1.flux_balance_info()
     assert b1 == b0 and abs(a1) < 1e-5 * max(1.0, abs(b1)) and s1 != 0.0
+
+
+@pytest.mark.parametrize("nsteps", [1, 2])
+def test_two_cell_forced_path_on_a_large_lattice(nsteps):
+    """FP32 lattices of at least 2^21 cells update two cells per thread, forced ones too: a uniform
+    body force and Coriolis (App. E), top sponge and lateral buffers, flux-balanced equilibrium cells through the paired
+    forced collision and nudging, against the oracle population by population (both step kinds)."""
+    faces = FACE_SETS[1]
+    case = synth.random_small_case(128, 128, 130, faces, seed=23, solid_fraction=0.04, margin=0)
+    assert case.solid.size >= 1 << 21
+    omega, force = (2e-3, -1e-3, 3e-3), (1e-5, 0.0, -2e-5)
+    sponge, buffer = (4, 0.3), (3, 0.25)
+    dom = _gpu(case, sponge=sponge, buffer=buffer, flux_balance=True, coriolis=omega, force=force)
+    dom.step(nsteps)
+    g = dom.export_populations().cpu().numpy()
+    kind, ub = oracle_inputs(case)
+    ueq, _, _, _ = zones.flux_balanced_ueq(kind, faces, ub)
+    F = orc.init(kind, ub, f64_of_f32(case.rho0), f64_of_f32(case.u0), ueq=ueq)
+    for _ in range(nsteps):
+        F = orc.step(F, kind, faces, ub, case.tau, case.cs, force=f64_of_f32(force), omega=f64_of_f32(omega), ueq=ueq)
+        F = zones.nudge(F, kind, faces, ub, sponge=sponge, buffer=buffer)
+    _, wo, _ = orc.lattice()
+    G = g[lib_to_oracle_order()] + wo[:, None, None, None]
+    diff = np.abs(G - F)[:, kind != orc.SOLID]
+    print(f"large lattice, forced two-cell path, {nsteps} steps: max |diff| = {diff.max():.2e}")
+    assert diff.max() <= 2e-6, diff.max()
