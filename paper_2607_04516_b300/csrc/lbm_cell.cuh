@@ -650,16 +650,35 @@ LBM_HD void eq_lanes_packed(const StepArgs &a, long long n0, long long n1, uint8
     }
 }
 
-// pk: the pair's 19 words (input), f0 / f1: its flags
+// Forced collision of a 16-bit pair held as packed words n0, n1 (decoded to plain populations,
+// through collide2_forced and nudge2, equilibrium lanes overwritten, encoded back).
 template <int S>
+LBM_HD void collide2_packed_forced(const StepArgs &a, int n0, int n1, uint8_t f0, uint8_t f1, uint32_t (&pk)[Q]) {
+    using Cd = Codec<S>;
+    float2 g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = Cd::template dec2<0>(pk[i]);
+    const float2 drho = collide2_forced<0>(g, a);
+    nudge2(a, n0, n1, drho, g);
+    if ((f0 | f1) & F_EQ) eq_lanes<0>(a, n0, n1, f0, f1, g);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) pk[i] = Cd::template enc2<0>(g[i]);
+}
+
+// pk: the pair's 19 words (input), f0 / f1: its flags
+template <int S, bool FORCE = false>
 LBM_HD void cellp_local_dual_body(const StepArgs &a, int n0, uint32_t (&pk)[Q], uint8_t f0, uint8_t f1) {
     using Cd = Codec<S>;
     using T = typename Cd::T;
     constexpr int LS = Cd::kLog2;
     const int m = n0 >> 1;
     if ((f0 & f1) & F_SOLID) return;
-    collide2_packed<S>(pk, a);
-    if ((f0 | f1) & F_EQ) eq_lanes_packed<S>(a, n0, n0 + 1, f0, f1, pk);
+    if constexpr (FORCE) {
+        collide2_packed_forced<S>(a, n0, n0 + 1, f0, f1, pk);
+    } else {
+        collide2_packed<S>(pk, a);
+        if ((f0 | f1) & F_EQ) eq_lanes_packed<S>(a, n0, n0 + 1, f0, f1, pk);
+    }
     if ((f0 | f1) & F_ZG) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -696,15 +715,14 @@ LBM_HD void cellp_local_dual_body(const StepArgs &a, int n0, uint32_t (&pk)[Q], 
 }
 
 // pk: the gathered pair (low half: cell n0), f0 / f1: flags (F_SOLID for a cell that does not exist)
-template <int S>
+template <int S, bool FORCE = false>
 LBM_HD void cell2_neighbor_interior_dual_body(const StepArgs &a, int n0, int n1, uint32_t (&pk)[Q], uint8_t f0,
                                               uint8_t f1) {
-    using Cd = Codec<S>;
-    constexpr int LS = Cd::kLog2;
     unsigned short *const *P = (unsigned short *const *)a.plane;
     const bool l0 = !(f0 & (F_SOLID | F_FACE)), l1 = !(f1 & (F_SOLID | F_FACE));
     if (!l0 && !l1) return;
-    collide2_packed<S>(pk, a);
+    if constexpr (FORCE) collide2_packed_forced<S>(a, n0, n1, 0, 0, pk);   // interior cells: no equilibrium lanes
+    else collide2_packed<S>(pk, a);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         if (!(c ? l1 : l0)) continue;
@@ -724,16 +742,16 @@ LBM_HD void cell2_neighbor_interior_dual_body(const StepArgs &a, int n0, int n1,
     }
 }
 
-template <int S>
+template <int S, bool FORCE = false>
 LBM_HD void cellp_local_dual(const StepArgs &a, int n0) {
     const int m = n0 >> 1;
     uint32_t pk[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) pk[i] = ld_early_u32((const uint32_t *)a.plane[i] + m);   // before the flags
-    cellp_local_dual_body<S>(a, n0, pk, a.flags[n0], a.flags[n0 + 1]);
+    cellp_local_dual_body<S, FORCE>(a, n0, pk, a.flags[n0], a.flags[n0 + 1]);
 }
 
-template <int S>
+template <int S, bool FORCE = false>
 LBM_HD void cell2_neighbor_interior_dual(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
     const unsigned short *const *P = (const unsigned short *const *)a.plane;
     uint32_t pk[Q];   // loaded before the flags are known (guard region after the planes)
@@ -742,7 +760,7 @@ LBM_HD void cell2_neighbor_interior_dual(const StepArgs &a, int n0, int n1, bool
         const unsigned short *p = P[opp(i)] - a.off[i];
         pk[i] = ld_early_u16(p + n0) | (ld_early_u16(p + n1) << 16);
     }
-    cell2_neighbor_interior_dual_body<S>(a, n0, n1, pk, v0 ? a.flags[n0] : F_SOLID, v1 ? a.flags[n1] : F_SOLID);
+    cell2_neighbor_interior_dual_body<S, FORCE>(a, n0, n1, pk, v0 ? a.flags[n0] : F_SOLID, v1 ? a.flags[n1] : F_SOLID);
 }
 
 // ---------------------------------------------------------------- FP32 storage, two cells at once
@@ -963,7 +981,7 @@ __device__ __forceinline__ void local_block(const StepArgs &a, unsigned bid) {
     } else if constexpr (PACK) {
         const int n0 = (int)(bid * 2 * kBlock + 2 * threadIdx.x);
         if (n0 >= a.g.N) return;
-        if constexpr (!FORCE && kDual16) cellp_local_dual<S>(a, n0);
+        if constexpr (kDual16) cellp_local_dual<S, FORCE>(a, n0);
         else cellp_local<S, FORCE>(a, n0);
     } else {
         const int n0 = (int)(bid * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
@@ -990,7 +1008,7 @@ __device__ __forceinline__ void neighbor_block(const StepArgs &a, unsigned bid, 
         } else {
             const int n0 = (int)((bid - face_blocks) * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
             if (n0 >= a.g.N) return;
-            if constexpr (!FORCE && kDual16) cell2_neighbor_interior_dual<S>(a, n0, n1, true, n1 < a.g.N);
+            if constexpr (kDual16) cell2_neighbor_interior_dual<S, FORCE>(a, n0, n1, true, n1 < a.g.N);
             else cell2_neighbor_interior<S, FORCE>(a, n0, n1, true, n1 < a.g.N);
         }
     } else {

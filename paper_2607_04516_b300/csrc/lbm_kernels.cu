@@ -48,14 +48,18 @@ __global__ void k_init(StepArgs a, const float *__restrict__ rho, const float *_
 }
 
 // PACK (16-bit storage with N and nx even): adjacent cell pairs with 4-byte accesses
-// resident blocks per SM of the forced FP32 step kernels: their pair collision with the body force
+// resident blocks per SM of the forced step kernels: the FP32 pair collision with the body force
 // and the zone nudging spills heavily at 64 registers; at 80 (3 blocks) FP32 zones run 15% faster
-// on the 400 x 400 x 80 city, while the 16-bit forced kernels are faster at 4 blocks
+// on the 400 x 400 x 80 city.  The 16-bit forced kernels spill too at 64 registers but still run
+// faster at 4 blocks (zones 33.6 against 32.8 GLUPS at 3, same city)
 #ifndef LBM_MIN_BLOCKS_FORCED32
 #define LBM_MIN_BLOCKS_FORCED32 3
 #endif
+#ifndef LBM_MIN_BLOCKS_FORCED16
+#define LBM_MIN_BLOCKS_FORCED16 4
+#endif
 template <int S, bool FORCE> constexpr int min_blocks(int unforced) {
-    return (FORCE && S == LBM_F32) ? LBM_MIN_BLOCKS_FORCED32 : unforced;
+    return !FORCE ? unforced : (S == LBM_F32 ? LBM_MIN_BLOCKS_FORCED32 : LBM_MIN_BLOCKS_FORCED16);
 }
 
 template <int S, bool FORCE, bool PACK, bool D32>

@@ -100,3 +100,37 @@ def test_two_cell_forced_path_on_a_large_lattice(nsteps):
     diff = np.abs(G - F)[:, kind != orc.SOLID]
     print(f"large lattice, forced two-cell path, {nsteps} steps: max |diff| = {diff.max():.2e}")
     assert diff.max() <= 2e-6, diff.max()
+
+
+@pytest.mark.parametrize("store,tol_rel", [("f16s", 2.0 ** -11), ("bf16s", 2.0 ** -8)])
+@pytest.mark.parametrize("nx", [14, 13])
+@pytest.mark.parametrize("warm", [2, 3])
+def test_16bit_forced_pairs_with_zones_and_coriolis(store, tol_rel, nx, warm):
+    """16-bit storage takes the paired forced collision and nudging in both step kinds (adjacent
+    pairs in the local step when nx and N are even, else the (n, n + 256) pairs).  From the GPU's
+    own state after `warm` steps, one more step with a uniform force, Coriolis, sponge, buffers and
+    flux balancing against the oracle's step from the same populations: every population within
+    the storage rounding of its shifted value."""
+    faces = FACE_SETS[1]
+    case = synth.random_small_case(nx, 8, 6, faces, seed=24, solid_fraction=0.1, margin=0)
+    omega, force = (2e-3, -1e-3, 3e-3), (1e-5, 0.0, -2e-5)
+    sponge, buffer = (2, 0.3), (2, 0.25)
+    dom = _gpu(case, store, sponge=sponge, buffer=buffer, flux_balance=True, coriolis=omega, force=force)
+    dom.step(warm)
+    g0 = dom.export_populations().cpu().numpy().astype(np.float64)
+    dom.step(1)
+    g1 = dom.export_populations().cpu().numpy().astype(np.float64)
+    kind, ub = oracle_inputs(case)
+    ueq, _, _, _ = zones.flux_balanced_ueq(kind, faces, ub)
+    _, wo, _ = orc.lattice()
+    order = lib_to_oracle_order()
+    F = g0[order] + wo[:, None, None, None]
+    F = orc.step(F, kind, faces, ub, case.tau, case.cs, force=f64_of_f32(force), omega=f64_of_f32(omega), ueq=ueq)
+    F = zones.nudge(F, kind, faces, ub, sponge=sponge, buffer=buffer)
+    G = g1[order] + wo[:, None, None, None]
+    keep = kind != orc.SOLID
+    err = np.abs(G - F)[:, keep]
+    bound = 3e-7 + 2.0 * tol_rel * np.abs(F - wo[:, None, None, None])[:, keep]
+    worst = float((err / bound).max())
+    print(f"{store} nx={nx} warm={warm}: forced pairs, worst error / bound = {worst:.3f}")
+    assert worst <= 1.0
