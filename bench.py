@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--store", default="f32", choices=list(STORE_BYTES))
     ap.add_argument("--workload", default="city400", choices=list(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10,zones,adjoint,ensemble,precision",
+    ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10,zones,physics,physics_f16s,adjoint,ensemble,precision",
                     help="extra storage kinds timed after the main measurement ('' = none)")
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--adjoint-steps", type=int, default=2000,
@@ -537,6 +537,29 @@ def run_ours(args, rank, world):
             variants[st] = {"glups": g2, "vs_f32": g2 / value if args.store == "f32" else None,
                             "ms_per_step": t_ms / K2, "sponge": [10, 0.05], "buffer": [16, 0.02],
                             "flux_balance": list(d2.flux_balance_info())}
+            del d2
+            torch.cuda.empty_cache()
+            continue
+        if st in ("physics", "physics_f16s"):
+            # every per-step physics term of the solver at once: Coriolis at the city's latitude
+            # (23.1 deg N, 0.01 s steps, App. E), the relaxation zones and flux balancing as in the
+            # zones leg (Sec. 3), and the synthetic von Karman inflow every 10 steps (App. F)
+            from paper_2607_04516_b300 import synth
+            store = "f16s" if st == "physics_f16s" else "f32"
+            omega = lbm.lbm_coriolis_omega(23.1, 0.01)
+            d2 = build_domain(store, sponge=(10, 0.05), buffer=(16, 0.02), flux_balance=True,
+                              coriolis=tuple(omega))
+            d2.configure_stg(synth.stg_uniforms(64, seed=11), n_modes=64, length=20.0, intensity=0.1,
+                             stride=10, interpolate=True)
+            K2 = max(200, args.steps // 4)
+            t_ms, _, _, _, _ = time_steps(d2, K2, min(args.warmup, 200), world, None)
+            t_ms = max_over_ranks(t_ms, world)
+            g2 = weak_scaling_glups(N, K2, world, t_ms)
+            variants[st] = {"glups": g2, "vs_f32": g2 / value if args.store == "f32" else None,
+                            "ms_per_step": t_ms / K2, "store": store,
+                            "coriolis": [float(v) for v in omega], "sponge": [10, 0.05],
+                            "buffer": [16, 0.02], "flux_balance": True, "stg": {"modes": 64, "stride": 10},
+                            "nonfinite_after": int(d2.diagnostics()["nonfinite"])}
             del d2
             torch.cuda.empty_cache()
             continue

@@ -219,3 +219,33 @@ def test_city_400x400x80_equilibrium_cells_after_two_steps():
     assert eq.sum() > 50000
     err = np.abs(u[eq] - want[eq]).max()
     assert err <= 1e-7, err
+
+
+@pytest.mark.parametrize("nsteps", [1, 2, 5])
+def test_inflow_turbulence_with_coriolis_force_and_zones_populations(nsteps):
+    """All per-step physics terms at once, as in a production run: the turbulent inflow (App. F), a
+    uniform force and Coriolis (App. E), a top sponge and lateral buffers (Sec. 3); populations
+    element by element against the oracle, which nudges after each of its steps."""
+    from oracle import zones
+    kw = PARAMS[2]
+    case = _small_case(FACE_SETS[0], seed=47)
+    case.coriolis = (1e-3, -2e-3, 3e-3)
+    case.force = (1e-5, 0.0, -2e-5)
+    sponge, buffer = (2, 0.3), (2, 0.25)
+    rnd = synth.stg_uniforms(kw["n_modes"], seed=207)
+    dom = gpu_domain(case, "f32", sponge=sponge, buffer=buffer)
+    dom.configure_stg(rnd, **kw)
+    dom.step(nsteps)
+    g = dom.export_populations().cpu().numpy()
+    kind, ub = oracle_inputs(case)
+    P = _oracle_params(kw)
+    fz, om = f64_of_f32(case.force), f64_of_f32(case.coriolis)
+    F = orc.init(kind, ub, f64_of_f32(case.rho0), f64_of_f32(case.u0), case.rho_b)
+    for t in range(nsteps):
+        ueq = orc.stg(kind, case.faces, ub, P, rnd, t)
+        F = orc.step(F, kind, case.faces, ub, case.tau, case.cs, force=fz, rho_b=case.rho_b, omega=om, ueq=ueq)
+        F = zones.nudge(F, kind, case.faces, ub, sponge=sponge, buffer=buffer)
+    _, wo, _ = orc.lattice()
+    G = g[lib_to_oracle_order()] + wo[:, None, None, None]
+    diff = np.abs(G - F)[:, kind != orc.SOLID]
+    assert diff.max() <= 2e-6, diff.max()
