@@ -1039,8 +1039,9 @@ LBM_HD float zone_rate(const StepArgs &a, int x, int y, int z) {
 
 LBM_HD void nudge(const StepArgs &a, long long n, float (&g)[Q]) {
     if (a.sponge_top <= 0 && a.buffer_faces == 0) return;
-    int x, y, z;
-    cell_coords(a.g, n, x, y, z);
+    // coordinates by the precomputed divisors (cell indices stay below 2^31)
+    const int r = div_by((int)n, a.div_nx, a.shr_nx), x = (int)n - r * a.g.nx;
+    const int z = div_by(r, a.div_ny, a.shr_ny), y = r - z * a.g.ny;
     const float s = zone_rate(a, x, y, z);
     if (s <= 0.0f) return;
     float drho = 0.0f;
