@@ -212,8 +212,10 @@ def e2e_glups(dom, case, steps: int, world: int):
     (lbm_set_inflow_profile, level speeds from pinned host memory), one lbm_step, and 8
     virtual-lidar columns x 10 heights come back device -> pinned host (lbm_sample_columns + an
     asynchronous copy into that step's row of a pinned host array).  The host does not wait per
-    step (a serving loop keeps the GPU busy); the timed region ends when every step's copy has
-    landed (one stream synchronisation)."""
+    step (a serving loop keeps the GPU busy).  The read-back runs on a second stream, from a ring of
+    four device sample buffers, so it overlaps the next step; a buffer is sampled into again only
+    after its copy has been ordered (stream waits on events, no host wait).  The timed region ends
+    when every step's copy has landed."""
     import numpy as np
     import torch
     nz, ny, nx = case.shape
@@ -223,26 +225,41 @@ def e2e_glups(dom, case, steps: int, world: int):
                   if not case.solid[0, y, x]][:8]
     ij = torch.tensor(fluid_cols, dtype=torch.int32, device=dom.device)
     kk = torch.tensor([min(nz - 1, 4 * (i + 1)) for i in range(10)], dtype=torch.int32, device=dom.device)
-    out_d = torch.empty((len(fluid_cols), 10, 4), dtype=torch.float32, device=dom.device)
+    ring = [torch.empty((len(fluid_cols), 10, 4), dtype=torch.float32, device=dom.device) for _ in range(4)]
+    out_d = ring[0]
     out_h = torch.empty((steps,) + tuple(out_d.shape), dtype=torch.float32).pin_memory()
     from paper_2607_04516_b300 import lbm
     speed_np = speed.numpy()
+    copy_stream = torch.cuda.Stream(device=dom.device)
+    sampled = [torch.cuda.Event() for _ in ring]
+    copied = [torch.cuda.Event() for _ in ring]
+
+    def one_step(k):
+        b = k % len(ring)
+        dom.set_inflow_profile(speed_np, case.theta)
+        dom.step(1)
+        if k >= len(ring):
+            dom.stream.wait_event(copied[b])           # its previous copy has read the buffer
+        lbm.lbm_sample_columns(dom.dom, ij, kk, ring[b])
+        sampled[b].record(dom.stream)
+        copy_stream.wait_event(sampled[b])
+        with torch.cuda.stream(copy_stream):
+            out_h[k].copy_(ring[b], non_blocking=True)
+        copied[b].record(copy_stream)
+
     with torch.cuda.stream(dom.stream):
         for k in range(min(10, steps)):
-            dom.set_inflow_profile(speed_np, case.theta)
-            dom.step(1)
-            dom.sample_columns(ij, kk, out_d)
-            out_h[k].copy_(out_d, non_blocking=True)
+            one_step(k)
         dom.stream.synchronize()
+        copy_stream.synchronize()
         barrier(world)
         t0 = time.perf_counter()
         for k in range(steps):
-            dom.set_inflow_profile(speed_np, case.theta)
-            dom.step(1)
-            lbm.lbm_sample_columns(dom.dom, ij, kk, out_d)
-            out_h[k].copy_(out_d, non_blocking=True)
+            one_step(k)
         dom.stream.synchronize()
+        copy_stream.synchronize()
         dt = time.perf_counter() - t0
+    out_d = ring[(steps - 1) % len(ring)]
     if not np.isfinite(out_h[-1].numpy()).all():
         raise RuntimeError("e2e: non-finite lidar samples")
     dt = max_over_ranks(dt, world)
