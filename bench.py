@@ -116,6 +116,15 @@ class ClockSampler:
         except OSError:
             self.p = None
 
+    def rows(self) -> int:
+        """Samples written so far."""
+        self.f.flush()
+        try:
+            with open(self.f.name) as f:
+                return sum(1 for r in f if r.strip())
+        except OSError:
+            return 0
+
     def stop(self):
         if self.p is None:
             return None
@@ -185,10 +194,17 @@ def time_steps(dom, K: int, W: int, world: int, clock_id: str | None):
     import torch
     dom.step(W)
     torch.cuda.synchronize()
-    barrier(world)
-    torch.cuda.synchronize()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
     sampler = ClockSampler(clock_id) if clock_id else None
+    # the clock record starts with at least 0.6 s (and 3 samples) of untimed steps under load right
+    # before the timed region, so that a short timed region still carries one (every rank runs them)
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < 0.6 or (sampler is not None and sampler.p is not None
+                                             and sampler.rows() < 3 and time.perf_counter() - t0 < 10.0):
+        dom.step(64)
+        torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
     t_wall = time.perf_counter()
     parity0 = dom.steps_done % 2
     evs[0].record(dom.stream)
@@ -198,6 +214,8 @@ def time_steps(dom, K: int, W: int, world: int, clock_id: str | None):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop() if sampler else None
+    if clocks is not None:
+        clocks["window"] = "from 0.6 s of untimed steps right before the timed region to its end"
     barrier(world)
     total_ms = evs[0].elapsed_time(evs[K])
     per = [evs[k].elapsed_time(evs[k + 1]) for k in range(K)]
@@ -452,6 +470,9 @@ def precision_leg(world: int):
         u = u.cpu().numpy().astype(np.float64)
         vs64[store] = float(np.linalg.norm((u - ur)[fl]) / np.linalg.norm(ur[fl]))
     out["cube64x64x32_u_rel_l2_vs_fp64_200"] = vs64
+    # the stated bound on that error: 1e-5 for FP32 storage, 1e-3 for 16-bit storage
+    bound = {"f32": 1e-5, "f16s": 1e-3, "bf16s": 1e-3}
+    out["meets_u_bound_vs_fp64"] = {s: {"bound": bound[s], "meets": vs64[s] <= bound[s]} for s in vs64}
     return out
 
 

@@ -141,7 +141,7 @@ size_t lbm_workspace_bytes(int nx, int ny, int nz, const lbm_params *p);
  *   solid      HOST array of nx*ny*nz bytes, x fastest, nonzero = solid (voxelised buildings,
  *              Sec. 2.1); copied during the call, may be freed afterwards
  *   nx,ny,nz   lattice size; >= 2 on every non-periodic axis, >= 1 on periodic ones,
- *              nx*ny*nz <= 2^31 - 1
+ *              nx*ny*nz + 2 (nx*ny + nx + 1) + 1024 < 2^31 (32-bit cell offsets in the kernels)
  *   workspace  DEVICE pointer, 256-byte aligned, ws_bytes >= lbm_workspace_bytes()
  *   stream     cudaStream_t as void* (NULL = default stream); all later calls use it
  *   out        receives the handle
@@ -218,7 +218,9 @@ int lbm_direction_table(int *c, float *w);
  *            outflow) face layer
  *   out[2] = max |u| over fluid cells
  *   out[3] = number of fluid cells with a non-finite population
- * Synchronises the domain's stream. */
+ * Each GPU thread sums the density deviations rho - 1 of its cells in FP32 (they are ~1e-3, so
+ * its partial keeps ~1e-10 of the mass) and max |u| in FP32; every sum across threads and blocks,
+ * and the flux, is FP64.  Synchronises the domain's stream. */
 lbm_status lbm_diagnostics(lbm_domain *d, double *out);
 
 /* The same reductions as lbm_diagnostics, for callers that must not allocate device memory and
@@ -231,8 +233,10 @@ lbm_status lbm_diagnostics(lbm_domain *d, double *out);
  * larger lattices return LBM_EINVAL.  All calls share that array: calls whose kernels overlap on
  * the GPU (different streams or host threads) race, so keep them in one stream order.  The first
  * call on a device looks up the array's device address; make it before any stream capture.  The
- * partial sums are added in a different order than in lbm_diagnostics, so the two agree to FP64
- * rounding, not bit for bit. */
+ * current CUDA device must be the one that was current at lbm_create_domain (else LBM_EINVAL):
+ * the array's address differs per device.  The threads take their cells in a different order
+ * than in lbm_diagnostics, so the masses agree to the rounding of the per-thread FP32 partials
+ * (~1e-10 relative), the flux to FP64 rounding, max |u| and the count exactly. */
 lbm_status lbm_diagnostics_noalloc(lbm_domain *d, double *out);
 
 /* ---------------------------------------------------------------------------------------------

@@ -37,7 +37,10 @@ const char *check_args(int nx, int ny, int nz, const lbm_params *p) {
     if (!p) return "params is NULL";
     if (nx < 1 || ny < 1 || nz < 1) return "lattice dimensions must be >= 1";
     const long long N = (long long)nx * ny * nz;
-    if (N > INT_MAX) return "nx*ny*nz exceeds 2^31-1 cells";
+    // the step kernels index cells with 32-bit integers: a cell index, plus the 256-cell offset of
+    // a thread's second cell, plus a neighbour offset (one z-plane and one row) must stay below 2^31
+    if (N + 2 * ((long long)nx * ny + nx + 1) + 1024 > INT_MAX)
+        return "lattice too large: nx*ny*nz + 2 (nx*ny + nx + 1) + 1024 must stay below 2^31";
     if (!(p->tau > 0.5f) || !std::isfinite(p->tau)) return "tau must be a finite value > 1/2";
     if (!(p->cs_smag >= 0.0f) || !std::isfinite(p->cs_smag)) return "cs_smag must be finite and >= 0";
     if (!(p->rho_b > 0.0f) || !std::isfinite(p->rho_b)) return "rho_b must be finite and > 0";
@@ -107,6 +110,7 @@ Layout make_layout(int nx, int ny, int nz, const lbm_params *p) {
 
 struct lbm_domain {
     int nx, ny, nz;
+    int device;                  // CUDA device current at creation (the workspace's device)
     long long N;
     lbm_params p;
     cudaStream_t stream;
@@ -296,7 +300,7 @@ void profile_level_weights(int L, int nz, int k, int &l0, int &l1, double &w1) {
     w1 = pos - l0;
 }
 DomainView domain_view(const lbm_domain *d) {
-    return DomainView{args_of(d), d->p.store, (d->t & 1) != 0, d->stream};
+    return DomainView{args_of(d), d->p.store, (d->t & 1) != 0, d->stream, d->device};
 }
 lbm_status domain_fail(lbm_domain *d, lbm_status st, const char *msg) { return fail(d, st, "%s", msg); }
 void domain_advance(lbm_domain *d, long long n) { d->t += n; }
@@ -380,6 +384,12 @@ lbm_status lbm_create_domain(const uint8_t *solid, int nx, int ny, int nz, const
     lbm_domain *d = new (std::nothrow) lbm_domain();
     if (!d) return LBM_ENOMEM;
     d->nx = nx; d->ny = ny; d->nz = nz;
+    d->device = 0;
+    if (cudaGetDevice(&d->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete d;
+        return LBM_ECUDA;
+    }
     d->N = (long long)nx * ny * nz;
     d->p = *p;
     d->stream = (cudaStream_t)stream;

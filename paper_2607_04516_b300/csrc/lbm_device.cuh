@@ -449,8 +449,16 @@ LBM_HD float2 fms2(float2 a, float2 b, float2 c) { return fma2(make_float2(-a.x,
 // moments are accumulated pair by pair (s = g_i + g_i+1, d = g_i - g_i+1 of each opposite pair),
 // so that besides the populations only the ten running moments are live; the relaxation then
 // visits each direction once more.
+// Relaxation coefficients of a pair of cells.  With LBM_RELAX_FOLD the rate om is folded into the
+// equilibrium coefficients: g* = (1 - om) g + om g^eq, so that om1 = 1 - om and e*, q*, a* (and
+// na* = -a*) already carry the factor om; otherwise g* = g + om (g^eq - g).  The two forms are the
+// same arithmetic (Eq. D.2) up to FP32 rounding; the folded one takes 6 instead of 9 FP32x2
+// instructions per opposite pair.
+#ifndef LBM_RELAX_FOLD
+#define LBM_RELAX_FOLD 1
+#endif
 struct Relax2 {
-    float2 om, ux, uy, uz, e0, e1, q1, a1, e2, q2, a2;
+    float2 om, ux, uy, uz, e0, e1, q1, a1, e2, q2, a2, na1, na2;
 };
 
 template <int LOG2S, class Get>
@@ -493,36 +501,70 @@ LBM_HD Relax2 collide2_moments(Get get, const StepArgs &a) {
         const float2 u = get(17), w = get(18), s_ = add2(u, w), d_ = sub2(u, w);
         m0 = add2(m0, s_); jy = add2(jy, d_); jz = sub2(jz, d_); syy = add2(syy, s_); szz = add2(szz, s_); syz = sub2(syz, s_);
     }
-    const float2 is = v2(iS);
-    const float2 drho = mul2(is, m0);
-    jx = mul2(is, jx); jy = mul2(is, jy); jz = mul2(is, jz);
-    sxx = mul2(is, sxx); syy = mul2(is, syy); szz = mul2(is, szz);
-    sxy = mul2(is, sxy); sxz = mul2(is, sxz); syz = mul2(is, syz);
+    // the moments stay at the storage scale S: u = j (1/S) / rho, and the stress Pi carries the
+    // factor S into Q, which the coefficient of Q under the square root takes back (S a power of 2)
+    const float2 drho = LOG2S ? mul2(v2(iS), m0) : m0;
     const float2 rho = add2(v2(1.0f), drho);
     Relax2 r;
     // IEEE division and square roots here (measured faster than the special-function forms when
     // both lanes go through them together)
     const float2 irho = make_float2(1.0f / rho.x, 1.0f / rho.y);
-    r.ux = mul2(jx, irho); r.uy = mul2(jy, irho); r.uz = mul2(jz, irho);
-    const float2 d3r = mul2(drho, v2(1.0f / 3.0f));
+    const float2 irs = LOG2S ? mul2(v2(iS), irho) : irho;
+    r.ux = mul2(jx, irs); r.uy = mul2(jy, irs); r.uz = mul2(jz, irs);
+    const float2 d3r = mul2(m0, v2(1.0f / 3.0f));
     const float2 pxx = fms2(jx, r.ux, sub2(sxx, d3r)), pyy = fms2(jy, r.uy, sub2(syy, d3r)),
                  pzz = fms2(jz, r.uz, sub2(szz, d3r));
     const float2 pxy = fms2(jx, r.uy, sxy), pxz = fms2(jx, r.uz, sxz), pyz = fms2(jy, r.uz, syz);
     const float2 pd = fma2(pzz, pzz, fma2(pyy, pyy, mul2(pxx, pxx)));
     const float2 po = fma2(pyz, pyz, fma2(pxz, pxz, mul2(pxy, pxy)));
-    const float2 pp2 = fma2(v2(4.0f), po, mul2(v2(2.0f), pd));   // 2 Pi:Pi
-    const float2 arg = fma2(mul2(v2(a.c2x18), irho), make_float2(sqrtf(pp2.x), sqrtf(pp2.y)), v2(a.tau * a.tau));
-    r.om = make_float2(2.0f / (a.tau + sqrtf(arg.x)), 2.0f / (a.tau + sqrtf(arg.y)));
+    const float2 pp2 = fma2(v2(4.0f), po, mul2(v2(2.0f), pd));   // 2 Pi:Pi (times S^2)
+    const float2 arg = fma2(mul2(v2(a.c2x18 * iS), irho), make_float2(sqrtf(pp2.x), sqrtf(pp2.y)), v2(a.tau * a.tau));
+    const float2 om = make_float2(2.0f / (a.tau + sqrtf(arg.x)), 2.0f / (a.tau + sqrtf(arg.y)));
     const float2 uu = fma2(r.uz, r.uz, fma2(r.uy, r.uy, mul2(r.ux, r.ux)));
     const float2 e = fms2(mul2(v2(1.5f), rho), uu, drho);
-    r.e0 = mul2(v2(S / 3.0f), e);
-    r.e1 = mul2(v2(S / 18.0f), e); r.q1 = mul2(v2(0.25f * S), rho); r.a1 = mul2(v2(S / 6.0f), rho);
-    r.e2 = mul2(v2(S / 36.0f), e); r.q2 = mul2(v2(0.125f * S), rho); r.a2 = mul2(v2(S / 12.0f), rho);
+    if (LBM_RELAX_FOLD) {
+        r.om = sub2(v2(1.0f), om);   // 1 - om
+        const float2 oe = mul2(om, e), orho = mul2(om, rho);
+        r.e0 = mul2(v2(S / 3.0f), oe);
+        r.e1 = mul2(v2(S / 18.0f), oe); r.q1 = mul2(v2(0.25f * S), orho); r.a1 = mul2(v2(S / 6.0f), orho);
+        r.e2 = mul2(v2(S / 36.0f), oe); r.q2 = mul2(v2(0.125f * S), orho); r.a2 = mul2(v2(S / 12.0f), orho);
+        r.na1 = mul2(v2(-S / 6.0f), orho); r.na2 = mul2(v2(-S / 12.0f), orho);
+    } else {
+        r.om = om;
+        r.e0 = mul2(v2(S / 3.0f), e);
+        r.e1 = mul2(v2(S / 18.0f), e); r.q1 = mul2(v2(0.25f * S), rho); r.a1 = mul2(v2(S / 6.0f), rho);
+        r.e2 = mul2(v2(S / 36.0f), e); r.q2 = mul2(v2(0.125f * S), rho); r.a2 = mul2(v2(S / 12.0f), rho);
+    }
     return r;
 }
 
 template <class Get, class Put>
 LBM_HD void collide2_relax(const Relax2 &r, Get get, Put put) {
+    if (LBM_RELAX_FOLD) {
+        {
+            const float2 g0 = get(0);
+            put(0, fma2(r.om, g0, r.e0));
+        }
+#define LBM_PAIR2(I, CU, E, Qc, Ac, NAc)                             \
+        {                                                           \
+            const float2 cu_ = (CU);                                \
+            const float2 sym_ = fma2(mul2(Qc, cu_), cu_, E);        \
+            const float2 gi_ = get(I), gj_ = get(I + 1);            \
+            put(I, fma2(r.om, gi_, fma2(Ac, cu_, sym_)));           \
+            put(I + 1, fma2(r.om, gj_, fma2(NAc, cu_, sym_)));      \
+        }
+        LBM_PAIR2(1, r.ux, r.e1, r.q1, r.a1, r.na1)
+        LBM_PAIR2(3, r.uy, r.e1, r.q1, r.a1, r.na1)
+        LBM_PAIR2(5, r.uz, r.e1, r.q1, r.a1, r.na1)
+        LBM_PAIR2(7, add2(r.ux, r.uy), r.e2, r.q2, r.a2, r.na2)
+        LBM_PAIR2(9, add2(r.ux, r.uz), r.e2, r.q2, r.a2, r.na2)
+        LBM_PAIR2(11, add2(r.uy, r.uz), r.e2, r.q2, r.a2, r.na2)
+        LBM_PAIR2(13, sub2(r.ux, r.uy), r.e2, r.q2, r.a2, r.na2)
+        LBM_PAIR2(15, sub2(r.ux, r.uz), r.e2, r.q2, r.a2, r.na2)
+        LBM_PAIR2(17, sub2(r.uy, r.uz), r.e2, r.q2, r.a2, r.na2)
+#undef LBM_PAIR2
+        return;
+    }
     {
         const float2 g0 = get(0);
         put(0, fma2(r.om, sub2(r.e0, g0), g0));
@@ -562,32 +604,63 @@ LBM_HD void collide2(float2 (&g)[Q], const StepArgs &a) {
     const float2 s13 = add2(g[13], g[14]), d13 = sub2(g[13], g[14]);
     const float2 s15 = add2(g[15], g[16]), d15 = sub2(g[15], g[16]);
     const float2 s17 = add2(g[17], g[18]), d17 = sub2(g[17], g[18]);
-    const float2 is = v2(iS);
-    const float2 drho = mul2(is, add2(add2(add2(g[0], add2(add2(s1, s3), s5)), add2(add2(s7, s9), add2(s11, s13))),
-                                      add2(s15, s17)));
-    const float2 jx = mul2(is, add2(add2(add2(add2(d1, d7), d9), d13), d15));
-    const float2 jy = mul2(is, add2(sub2(add2(add2(d3, d7), d11), d13), d17));
-    const float2 jz = mul2(is, sub2(sub2(add2(add2(d5, d9), d11), d15), d17));
-    const float2 sxx = mul2(is, add2(add2(add2(add2(s1, s7), s9), s13), s15));
-    const float2 syy = mul2(is, add2(add2(add2(add2(s3, s7), s11), s13), s17));
-    const float2 szz = mul2(is, add2(add2(add2(add2(s5, s9), s11), s15), s17));
-    const float2 sxy = mul2(is, sub2(s7, s13)), sxz = mul2(is, sub2(s9, s15)), syz = mul2(is, sub2(s11, s17));
+    const float2 m0 = add2(add2(add2(g[0], add2(add2(s1, s3), s5)), add2(add2(s7, s9), add2(s11, s13))),
+                           add2(s15, s17));
+    // moments at the storage scale S (see collide2_moments)
+    const float2 jx = add2(add2(add2(add2(d1, d7), d9), d13), d15);
+    const float2 jy = add2(sub2(add2(add2(d3, d7), d11), d13), d17);
+    const float2 jz = sub2(sub2(add2(add2(d5, d9), d11), d15), d17);
+    const float2 sxx = add2(add2(add2(add2(s1, s7), s9), s13), s15);
+    const float2 syy = add2(add2(add2(add2(s3, s7), s11), s13), s17);
+    const float2 szz = add2(add2(add2(add2(s5, s9), s11), s15), s17);
+    const float2 sxy = sub2(s7, s13), sxz = sub2(s9, s15), syz = sub2(s11, s17);
+    const float2 drho = LOG2S ? mul2(v2(iS), m0) : m0;
     const float2 rho = add2(v2(1.0f), drho);
     // IEEE division and square roots here (measured faster than the special-function forms when
     // both lanes go through them together)
     const float2 irho = make_float2(1.0f / rho.x, 1.0f / rho.y);
-    const float2 ux = mul2(jx, irho), uy = mul2(jy, irho), uz = mul2(jz, irho);
-    const float2 d3r = mul2(drho, v2(1.0f / 3.0f));
+    const float2 irs = LOG2S ? mul2(v2(iS), irho) : irho;
+    const float2 ux = mul2(jx, irs), uy = mul2(jy, irs), uz = mul2(jz, irs);
+    const float2 d3r = mul2(m0, v2(1.0f / 3.0f));
     const float2 pxx = fms2(jx, ux, sub2(sxx, d3r)), pyy = fms2(jy, uy, sub2(syy, d3r)),
                  pzz = fms2(jz, uz, sub2(szz, d3r));
     const float2 pxy = fms2(jx, uy, sxy), pxz = fms2(jx, uz, sxz), pyz = fms2(jy, uz, syz);
     const float2 pd = fma2(pzz, pzz, fma2(pyy, pyy, mul2(pxx, pxx)));
     const float2 po = fma2(pyz, pyz, fma2(pxz, pxz, mul2(pxy, pxy)));
-    const float2 pp2 = fma2(v2(4.0f), po, mul2(v2(2.0f), pd));   // 2 Pi:Pi
-    const float2 arg = fma2(mul2(v2(a.c2x18), irho), make_float2(sqrtf(pp2.x), sqrtf(pp2.y)), v2(a.tau * a.tau));
+    const float2 pp2 = fma2(v2(4.0f), po, mul2(v2(2.0f), pd));   // 2 Pi:Pi (times S^2)
+    const float2 arg = fma2(mul2(v2(a.c2x18 * iS), irho), make_float2(sqrtf(pp2.x), sqrtf(pp2.y)), v2(a.tau * a.tau));
     const float2 om = make_float2(2.0f / (a.tau + sqrtf(arg.x)), 2.0f / (a.tau + sqrtf(arg.y)));
     const float2 uu = fma2(uz, uz, fma2(uy, uy, mul2(ux, ux)));
     const float2 e = fms2(mul2(v2(1.5f), rho), uu, drho);
+    if (LBM_RELAX_FOLD) {
+        // g* = (1 - om) g + om g^eq with om folded into the equilibrium coefficients
+        const float2 om1 = sub2(v2(1.0f), om);
+        const float2 oe = mul2(om, e), orho = mul2(om, rho);
+        const float2 e0 = mul2(v2(S / 3.0f), oe);
+        const float2 e1 = mul2(v2(S / 18.0f), oe), q1 = mul2(v2(0.25f * S), orho), a1 = mul2(v2(S / 6.0f), orho),
+                     na1 = mul2(v2(-S / 6.0f), orho);
+        const float2 e2 = mul2(v2(S / 36.0f), oe), q2 = mul2(v2(0.125f * S), orho), a2 = mul2(v2(S / 12.0f), orho),
+                     na2 = mul2(v2(-S / 12.0f), orho);
+        g[0] = fma2(om1, g[0], e0);
+#define LBM_PAIR2(I, CU, E, Qc, Ac, NAc)                                \
+        {                                                               \
+            const float2 cu_ = (CU);                                    \
+            const float2 sym_ = fma2(mul2(Qc, cu_), cu_, E);            \
+            g[I] = fma2(om1, g[I], fma2(Ac, cu_, sym_));                \
+            g[I + 1] = fma2(om1, g[I + 1], fma2(NAc, cu_, sym_));       \
+        }
+        LBM_PAIR2(1, ux, e1, q1, a1, na1)
+        LBM_PAIR2(3, uy, e1, q1, a1, na1)
+        LBM_PAIR2(5, uz, e1, q1, a1, na1)
+        LBM_PAIR2(7, add2(ux, uy), e2, q2, a2, na2)
+        LBM_PAIR2(9, add2(ux, uz), e2, q2, a2, na2)
+        LBM_PAIR2(11, add2(uy, uz), e2, q2, a2, na2)
+        LBM_PAIR2(13, sub2(ux, uy), e2, q2, a2, na2)
+        LBM_PAIR2(15, sub2(ux, uz), e2, q2, a2, na2)
+        LBM_PAIR2(17, sub2(uy, uz), e2, q2, a2, na2)
+#undef LBM_PAIR2
+        return;
+    }
     const float2 e0 = mul2(v2(S / 3.0f), e);
     const float2 e1 = mul2(v2(S / 18.0f), e), q1 = mul2(v2(0.25f * S), rho), a1 = mul2(v2(S / 6.0f), rho);
     const float2 e2 = mul2(v2(S / 36.0f), e), q2 = mul2(v2(0.125f * S), rho), a2 = mul2(v2(S / 12.0f), rho);

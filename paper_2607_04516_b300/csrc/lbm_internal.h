@@ -28,6 +28,7 @@ struct DomainView {
     int store;
     bool layoutA;
     cudaStream_t stream;
+    int device;      // CUDA device of the domain's workspace
 };
 DomainView domain_view(const lbm_domain *d);
 // Level-to-height mapping of the inflow profile: s(z_k) = (1 - w1) speed[l0] + w1 speed[l1]

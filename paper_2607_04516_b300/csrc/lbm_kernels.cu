@@ -129,61 +129,17 @@ __global__ void k_export(StepArgs a, bool layoutA, float *__restrict__ out) {
 }
 
 // ---------------------------------------------------------------- FP64 diagnostics
-// Pass 1: kRedBlocks blocks stride over the lattice; each writes 4 partials into scratch.
+// Pass 1: kRedBlocks blocks stride over the lattice; each thread accumulates its cells (diag_cell:
+// FP32 partials of the small per-cell terms) and each block writes 4 FP64 partials into scratch.
 // Pass 2: one block folds the partials.  Fixed block count -> deterministic result.
 template <int S>
 __global__ void __launch_bounds__(kBlock) k_reduce_partial(StepArgs a, bool layoutA,
                                                            double *__restrict__ part) {
-    double mass = 0.0, flux = 0.0, umax = 0.0, bad = 0.0;
+    DiagAcc acc;
     const long long stride = (long long)gridDim.x * kBlock;
-    for (long long n = (long long)blockIdx.x * kBlock + threadIdx.x; n < a.g.N; n += stride) {
-        const uint8_t fl = a.flags[n];
-        if (fl & F_SOLID) continue;
-        float r, ux, uy, uz;
-        int x, y, z;
-        cell_coords(a.g, n, x, y, z);
-        if (fl & F_EQ) {
-            r = a.rho_b;
-            eq_velocity(a, x, y, z, ux, uy, uz);
-        } else {
-            float g[Q];
-            read_post<S>(a, n, fl, layoutA, g);
-            bool finite = true;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) finite &= isfinite(g[i]);
-            if (!finite) { bad += 1.0; continue; }
-            macros_of(a, g, r, ux, uy, uz);
-            mass += (double)r;
-            const double um = sqrt((double)ux * ux + (double)uy * uy + (double)uz * uz);
-            umax = um > umax ? um : umax;
-        }
-        // outward mass flux through every open face layer the cell lies on
-        const float uu[3] = {ux, uy, uz};
-        const int p[3] = {x, y, z};
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            const int fl0 = a.g.face[2 * ax], fl1 = a.g.face[2 * ax + 1];
-            const bool open0 = fl0 == LBM_FACE_INFLOW_EQ || fl0 == LBM_FACE_OUTFLOW_ZG;
-            const bool open1 = fl1 == LBM_FACE_INFLOW_EQ || fl1 == LBM_FACE_OUTFLOW_ZG;
-            if (open0 && p[ax] == 0) flux -= (double)r * uu[ax];
-            if (open1 && p[ax] == dim(a.g, ax) - 1) flux += (double)r * uu[ax];
-        }
-    }
-    __shared__ double sh[4][kBlock];
-    sh[0][threadIdx.x] = mass; sh[1][threadIdx.x] = flux;
-    sh[2][threadIdx.x] = umax; sh[3][threadIdx.x] = bad;
-    __syncthreads();
-    for (int s = kBlock / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
-            sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
-            sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + s]);
-            sh[3][threadIdx.x] += sh[3][threadIdx.x + s];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 4; ++k) part[4 * blockIdx.x + k] = sh[k][0];
+    for (long long n = (long long)blockIdx.x * kBlock + threadIdx.x; n < a.g.N; n += stride)
+        diag_cell<S>(a, n, layoutA, acc);
+    diag_block_store<kBlock>(acc, part + 4 * blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kBlock) k_reduce_final(const double *__restrict__ part, int nb,

@@ -66,59 +66,18 @@ cudaError_t scratch_for_current_device(double **out) {
 }
 
 // Pass 1: block b reduces the cells [b * kCellsPerBlock, (b + 1) * kCellsPerBlock) into
-// part[4b .. 4b+3]: the same per-cell quantities as lbm_diagnostics.
+// part[4b .. 4b+3], with the per-cell rule and the block fold of lbm_diagnostics (diag_cell,
+// diag_block_store).
 template <int S>
 __global__ void __launch_bounds__(kBlockNa) k_na_partial(StepArgs a, bool layoutA, double *__restrict__ part) {
-    double mass = 0.0, flux = 0.0, umax = 0.0, bad = 0.0;
+    DiagAcc acc;
     const long long base = (long long)blockIdx.x * kCellsPerBlock;
     for (int k = 0; k < kCellsPerThread; ++k) {
         const long long n = base + (long long)k * kBlockNa + threadIdx.x;
         if (n >= a.g.N) break;
-        const uint8_t fl = a.flags[n];
-        if (fl & F_SOLID) continue;
-        float r, ux, uy, uz;
-        int x, y, z;
-        cell_coords(a.g, n, x, y, z);
-        if (fl & F_EQ) {
-            r = a.rho_b;
-            eq_velocity(a, x, y, z, ux, uy, uz);
-        } else {
-            float g[Q];
-            read_post<S>(a, n, fl, layoutA, g);
-            bool finite = true;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) finite &= isfinite(g[i]);
-            if (!finite) { bad += 1.0; continue; }
-            macros_of(a, g, r, ux, uy, uz);
-            mass += (double)r;
-            const double um = sqrt((double)ux * ux + (double)uy * uy + (double)uz * uz);
-            umax = um > umax ? um : umax;
-        }
-        const float uu[3] = {ux, uy, uz};
-        const int p[3] = {x, y, z};
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            const int f0 = a.g.face[2 * ax], f1 = a.g.face[2 * ax + 1];
-            if ((f0 == LBM_FACE_INFLOW_EQ || f0 == LBM_FACE_OUTFLOW_ZG) && p[ax] == 0) flux -= (double)r * uu[ax];
-            if ((f1 == LBM_FACE_INFLOW_EQ || f1 == LBM_FACE_OUTFLOW_ZG) && p[ax] == dim(a.g, ax) - 1)
-                flux += (double)r * uu[ax];
-        }
+        diag_cell<S>(a, n, layoutA, acc);
     }
-    __shared__ double sh[4][kBlockNa];
-    sh[0][threadIdx.x] = mass; sh[1][threadIdx.x] = flux;
-    sh[2][threadIdx.x] = umax; sh[3][threadIdx.x] = bad;
-    __syncthreads();
-    for (int s = kBlockNa / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
-            sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
-            sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + s]);
-            sh[3][threadIdx.x] += sh[3][threadIdx.x + s];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 4; ++k) part[4 * blockIdx.x + k] = sh[k][0];
+    diag_block_store<kBlockNa>(acc, part + 4 * blockIdx.x);
 }
 
 // Pass 2: one block folds the nb partials into the caller's out[4].
@@ -165,8 +124,14 @@ extern "C" lbm_status lbm_diagnostics_noalloc(lbm_domain *d, double *out) {
         return domain_fail(d, LBM_EINVAL,
                            "diagnostics_noalloc: lattice has more than 2^28 cells, the limit of its "
                            "fixed 512 KiB scratch; use lbm_diagnostics");
+    // the scratch address is per device: the current device must be the domain's
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return domain_fail(d, LBM_ECUDA, cudaGetErrorString(e));
+    if (cur != v.device)
+        return domain_fail(d, LBM_EINVAL, "diagnostics_noalloc: the current CUDA device is not the domain's device");
     double *part = nullptr;
-    cudaError_t e = scratch_for_current_device(&part);
+    e = scratch_for_current_device(&part);
     if (e != cudaSuccess) return domain_fail(d, LBM_ECUDA, cudaGetErrorString(e));
     const int nb = (int)((v.args.g.N + kCellsPerBlock - 1) / kCellsPerBlock);
     switch (v.store) {

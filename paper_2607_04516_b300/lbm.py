@@ -240,8 +240,11 @@ def lbm_diagnostics(dom) -> dict:
 
 def lbm_diagnostics_noalloc(dom, out):
     """``out``: CUDA float64 tensor of 4 elements, filled asynchronously on the domain's stream."""
+    import torch
     if out.dtype.itemsize != 8 or out.numel() < 4 or not out.is_cuda:
         raise ValueError("out must be a CUDA float64 tensor with 4 elements")
+    if out.device.index != torch.cuda.current_device():
+        raise ValueError("out must live on the current CUDA device (the domain's device)")
     _check(load().lbm_diagnostics_noalloc(dom, _ptr(out)), dom)
 
 
@@ -447,6 +450,7 @@ class LidarProblem:
         self.params = make_adjoint_params(n_steps, n_avg, checkpoint_every)
         self.target = torch.as_tensor(np.asarray(target, np.float32), device=domain.device).contiguous()
         self._ws = {}
+        self.reverse_sweeps = 0       # calls that ran the reverse sweep (misfit_grad)
 
     def _workspace(self, grad: bool):
         import torch
@@ -469,6 +473,7 @@ class LidarProblem:
     def misfit_grad(self, speed, theta):
         """(J, dJ/d(speed..., theta) (L + 1,), mean) as CUDA float64 tensors."""
         import torch
+        self.reverse_sweeps += 1
         L = len(speed)
         out = torch.empty((L + 2,), dtype=torch.float64, device=self.domain.device)
         mean = torch.empty((len(self.cols), len(self.heights), 4), dtype=torch.float64, device=self.domain.device)
@@ -481,13 +486,17 @@ def _autograd_function():
     import torch
 
     class LidarMisfit(torch.autograd.Function):
-        """J(p) for p = (speed_0 .. speed_{L-1}, theta) (float64 tensor): the forward call runs the
-        forward model and the discrete adjoint together (``lbm_lidar_misfit_grad``); backward
-        returns the stored gradient times the incoming one."""
+        """J(p) for p = (speed_0 .. speed_{L-1}, theta) (float64 tensor): when p needs a gradient
+        the forward call runs the forward model and the discrete adjoint together
+        (``lbm_lidar_misfit_grad``) and backward returns the stored gradient times the incoming
+        one; otherwise only the forward model runs (``lbm_lidar_misfit``)."""
 
         @staticmethod
         def forward(ctx, p, problem):
             pc = p.detach().to("cpu", torch.float64).numpy()
+            if not ctx.needs_input_grad[0]:
+                J, _ = problem.misfit(pc[:-1], float(pc[-1]))
+                return J.to(p.device, p.dtype)
             J, grad, _ = problem.misfit_grad(pc[:-1], float(pc[-1]))
             ctx.save_for_backward(grad.to(p.device, p.dtype))
             return J.to(p.device, p.dtype)
@@ -501,7 +510,14 @@ def _autograd_function():
 
 
 def lidar_misfit(p, problem: LidarProblem):
-    """Differentiable J(p) (torch.autograd): ``p`` = (speed_0 .. speed_{L-1}, theta)."""
+    """Differentiable J(p) (torch.autograd): ``p`` = (speed_0 .. speed_{L-1}, theta).  Under
+    ``torch.no_grad()``, or for a ``p`` that does not require a gradient, only the forward model
+    runs (no reverse sweep)."""
+    import torch
+    if not (torch.is_grad_enabled() and p.requires_grad):
+        pc = p.detach().to("cpu", torch.float64).numpy()
+        J, _ = problem.misfit(pc[:-1], float(pc[-1]))
+        return J.to(p.device, p.dtype)
     global _LidarMisfit
     try:
         fn = _LidarMisfit

@@ -7,7 +7,16 @@ import numpy as np
 from oracle import oracle as orc
 from paper_2607_04516_b300 import synth
 
-TOL_U = {"f32": 1e-5, "f16s": 1e-3, "bf16s": 1e-2}   # relative L2 of u over fluid cells
+# Relative L2 of u over fluid cells against the FP64 oracle, laminar cases after 200 steps.
+# TARGET_U is the bound the project states for each storage form: 1e-5 for FP32, 1e-3 for 16-bit
+# storage.  FP32 and FP16S meet it.  BF16S does not: BF16 keeps 8 significant bits, each store
+# rounds by up to 2^-9 relative, and over hundreds of steps that lands at a few 1e-3 (3.5e-3 on the
+# 64x64x32 cube).  Its tests therefore assert ENVELOPE_U, the measured error envelope of BF16S --
+# a regression guard, not the 16-bit target.  TOL_U is what the parity tests assert.
+TARGET_U = {"f32": 1e-5, "f16s": 1e-3, "bf16s": 1e-3}
+ENVELOPE_U = {"bf16s": 1e-2}
+TOL_U = {s: ENVELOPE_U.get(s, t) for s, t in TARGET_U.items()}
+MEETS_TARGET = {s: s not in ENVELOPE_U for s in TARGET_U}
 
 
 def f32(a):

@@ -116,6 +116,26 @@ def test_autograd_function_returns_the_adjoint_gradient():
     np.testing.assert_array_equal(p.grad.numpy(), 2.0 * g2.cpu().numpy())
 
 
+def test_autograd_function_skips_the_reverse_sweep_without_a_gradient():
+    """Under no_grad, or for a parameter tensor that needs no gradient, J comes from the forward
+    model alone (no reverse sweep) and equals the differentiable evaluation's value."""
+    import torch
+    from paper_2607_04516_b300 import lbm
+    faces = ("inflow", "outflow", "inflow", "outflow", "noslip", "freeslip")
+    solid, cols, hts = _small(faces)
+    gp = _gpu_problem(solid, faces, cols, hts, np.full((3, 3, 2), 0.03, np.float32), 20, 5, 6)
+    p = torch.tensor([0.04, 0.05, 0.045, 0.055, 0.3], dtype=torch.float64, requires_grad=True)
+    J = lbm.lidar_misfit(p, gp)
+    assert gp.reverse_sweeps == 1
+    with torch.no_grad():
+        J_ng = lbm.lidar_misfit(p, gp)
+    J_nr = lbm.lidar_misfit(p.detach(), gp)
+    torch.cuda.synchronize()
+    assert gp.reverse_sweeps == 1
+    assert not J_ng.requires_grad and not J_nr.requires_grad
+    assert float(J_ng) == float(J.detach()) == float(J_nr)
+
+
 def test_zero_misfit_gives_zero_gradient():
     import torch
     faces = ("inflow", "outflow", "periodic", "periodic", "noslip", "freeslip")

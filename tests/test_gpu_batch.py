@@ -128,3 +128,30 @@ def test_batch_rejects_mixed_members_and_parity():
     a.step(1)   # stepped outside the batch: parities differ
     with pytest.raises(lbm.LbmError):
         b.step(1)
+
+
+@pytest.mark.parametrize("store", ["f32", "f16s"])
+def test_batched_members_match_the_oracle_after_200_steps(store):
+    """Each member of a batch advanced by CUDA-graph replay of the batched kernel (200 steps)
+    against the FP64 oracle run of that member alone: relative L2 of u over fluid cells within the
+    parity bound of its storage (laminar cube flows of two sizes, one with odd nx)."""
+    import torch
+    from oracle import oracle as orc
+    from paper_2607_04516_b300 import lbm
+    from gpu_common import TOL_U, oracle_run, rel_l2
+    cases = [synth.cube_case(), synth.cube_case(nx=41, ny=24, nz=16)]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        doms = _domains(cases, store)
+        b = lbm.Batch(doms, stream=stream)
+        b.capture(100)
+        b.launch()
+        b.launch()
+        out = [d.macroscopic() for d in doms]
+    stream.synchronize()
+    for c, d, (rho, u) in zip(cases, doms, out):
+        assert d.steps_done == 200
+        _, ur, _, kind, _ = oracle_run(c, 200)
+        err = rel_l2(u.cpu().numpy().astype(np.float64), ur, kind == orc.FLUID)
+        print(f"batched {c.shape} {store}: rel L2 u vs FP64 oracle = {err:.2e}")
+        assert err <= TOL_U[store]

@@ -1,8 +1,9 @@
 """GPU parity: the sm_103a path through the C ABI against the FP64 oracle, element by element on
-the same seeded inputs.  Tolerances (relative L2 of velocity over fluid cells): FP32 1e-5,
-FP16S 1e-3 (the target stated for 16-bit storage), BF16S 1e-2 (BF16 keeps 8 significant bits:
-each store rounds by up to 2^-9 relative; over hundreds of steps that lands at a few 1e-3, so
-1e-3 is not reachable with f - w_i shifted BF16 and the bound below is the measured envelope)."""
+the same seeded inputs.  Tolerances (relative L2 of velocity over fluid cells): FP32 1e-5 and
+FP16S 1e-3, the targets stated for FP32 and 16-bit storage.  BF16S misses the 1e-3 target (BF16
+keeps 8 significant bits: each store rounds by up to 2^-9 relative; over hundreds of steps that
+lands at a few 1e-3); its tests assert the measured envelope 1e-2 instead, and
+test_bf16s_misses_the_16bit_target states that it does not meet 1e-3."""
 import math
 
 import numpy as np
@@ -11,7 +12,7 @@ import pytest
 from oracle import oracle as orc
 from paper_2607_04516_b300 import synth
 
-from gpu_common import (TOL_U, f32, gpu_domain, gpu_run, lib_to_oracle_order, oracle_inputs,
+from gpu_common import (MEETS_TARGET, TARGET_U, TOL_U, f32, gpu_domain, gpu_run, lib_to_oracle_order, oracle_inputs,
                         oracle_one_step_planes, oracle_run, rel_l2)
 
 pytestmark = pytest.mark.gpu
@@ -48,6 +49,18 @@ def test_cube_64x64x32(store, nsteps):
     print(f"cube {store} {nsteps} steps: rel L2 u = {err:.3e}, rho = {rel_l2(rho - 1, rr - 1, fl):.3e}")
     tol = TOL_U[store] * (2.0 if nsteps == 500 else 1.0)
     assert err <= tol
+
+
+def test_bf16s_misses_the_16bit_target():
+    """BF16S storage does not meet the 1e-3 bound of 16-bit storage on the cube after 200 steps
+    (only FP16S does); its parity tests assert the 1e-2 envelope.  Should BF16S ever meet the
+    bound, this test fails and the envelope goes."""
+    assert not MEETS_TARGET["bf16s"] and MEETS_TARGET["f16s"]
+    case = synth.cube_case()
+    _, u, _ = gpu_run(case, 200, "bf16s")
+    _, ur, _, kind, _ = _oracle_cached(("cube", 200), case, 200)
+    err = rel_l2(u, ur, kind == orc.FLUID)
+    assert TARGET_U["bf16s"] < err <= TOL_U["bf16s"]
 
 
 @pytest.mark.parametrize("cs", [0.0, 0.16])
