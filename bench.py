@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--store", default="f32", choices=list(STORE_BYTES))
     ap.add_argument("--workload", default="city400", choices=list(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10,zones,physics,physics_f16s,adjoint,ensemble,precision",
+    ap.add_argument("--variants", default="f16s,bf16s,stg,stg_s10,zones,physics,physics_f16s,adjoint,ensemble,ensemble_small,precision",
                     help="extra storage kinds timed after the main measurement ('' = none)")
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--adjoint-steps", type=int, default=2000,
@@ -351,16 +351,23 @@ def adjoint_leg(world: int, nsteps: int = 2000, iters: int = 20):
     return out
 
 
-def ensemble_leg(world: int, steps: int = 40):
-    """Batched ensemble: a wind rose of 16 inflow directions x 2 speeds on a 256x256x64 city plus 8
-    domains of uneven size (96x96x32 .. 320x192x64), FP32.  Aggregate GLUPS (all cells of all members
-    per second) of one single-domain launch per member and step, against the batched launch in the
+def ensemble_leg(world: int, steps: int = 40, small: bool = False):
+    """Batched ensemble, FP32.  Default workload: a wind rose of 16 inflow directions x 2 speeds on a
+    256x256x64 city plus 8 domains of uneven size (96x96x32 .. 320x192x64).  small: 12 directions x
+    2 speeds on a 96x96x32 city plus the same 8 uneven domains, where each member's own launch is
+    short and launch and tail overhead matter.  Aggregate GLUPS (all cells of all members per
+    second) of one single-domain launch per member and step, against the batched launch in the
     autotuned shape, stepped directly and replayed from a CUDA graph; CUDA events on the batch's
     stream."""
     import numpy as np
     import torch
     from paper_2607_04516_b300 import lbm, synth
-    cases = synth.ensemble_cases() + synth.uneven_cases()
+    if small:
+        cases = synth.ensemble_cases(nx=96, ny=96, nz=32, n_dir=12) + synth.uneven_cases()
+        label = "12 directions x 2 speeds on a 96x96x32 city (seed 3) + 8 uneven domains 96x96x32 .. 320x192x64"
+    else:
+        cases = synth.ensemble_cases() + synth.uneven_cases()
+        label = "16 directions x 2 speeds on a 256x256x64 city (seed 3) + 8 uneven domains 96x96x32 .. 320x192x64"
     cells = int(sum(c.solid.size for c in cases))
     stream = torch.cuda.Stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -381,7 +388,7 @@ def ensemble_leg(world: int, steps: int = 40):
             d.init_fields()
             doms.append(d)
         b = lbm.Batch(doms, stream=stream)
-        b.shape = 4
+        b.shape = 4                        # one single-domain launch per member
         b.step(2)
         seq = timed(lambda: b.step(steps))
         choice, tune_ms = b.autotune(trial_steps=10)
@@ -392,11 +399,10 @@ def ensemble_leg(world: int, steps: int = 40):
     barrier(world)
     seq, bat, gra = (max_over_ranks(x, world) for x in (seq, bat, gra))
     g = lambda ms: cells * steps * world / (ms / 1e3) / 1e9
-    out = {"workload": f"16 directions x 2 speeds on a 256x256x64 city (seed 3) + 8 uneven domains "
-                       f"96x96x32 .. 320x192x64; {len(cases)} members, {cells} cells, FP32",
+    out = {"workload": f"{label}; {len(cases)} members, {cells} cells, FP32",
            "steps": steps, "sequential_glups": g(seq), "batched_glups": g(bat), "graph_glups": g(gra),
            "graph_vs_sequential": seq / gra, "shape": lbm.BATCH_SHAPES[choice],
-           "autotune_ms_per_step": dict(zip(lbm.BATCH_SHAPES, tune_ms))}
+           "autotune_ms_per_step": {k: (v if v > 0 else None) for k, v in zip(lbm.BATCH_SHAPES, tune_ms)}}
     del b, doms
     torch.cuda.empty_cache()
     return out
@@ -559,6 +565,9 @@ def run_ours(args, rank, world):
             continue
         if st == "ensemble":
             variants[st] = ensemble_leg(world)
+            continue
+        if st == "ensemble_small":
+            variants[st] = ensemble_leg(world, small=True)
             continue
         if st == "precision":
             variants[st] = precision_leg(world)

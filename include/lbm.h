@@ -400,16 +400,23 @@ lbm_status lbm_batch_capture(lbm_batch *b, int nsteps);
  * when nothing is captured or the members are not at the parity of the capture. */
 lbm_status lbm_batch_launch(lbm_batch *b);
 
-/* Launch shapes: 0 = kernels compiled for 4 resident blocks per SM, members in the given order;
- * 1 = 3 blocks per SM, given order; 2 = 4 blocks, largest member first; 3 = 3 blocks, largest
- * first; 4 = one single-domain launch per member and step (no batching).  The autotuner runs
- * 2 + trial_steps steps of every shape on the members (they advance by 5 (2 + trial_steps)),
- * times each with CUDA events and keeps the fastest.  trial_steps even, >= 2.  choice (may be
- * NULL) receives the chosen shape, ms_per_step (may be NULL) five times in ms per step.
- * Synchronises the stream; drops a captured graph. */
+/* Launch shapes (lbm_batch_shape_count() of them).  Batched kernels with 256-thread blocks
+ * compiled for 4 resident blocks per SM, members in the given order, FP32 members with their own
+ * cells per thread (as lbm_step), unless stated: 0 = that; 1 = 3 blocks per SM; 2 = largest
+ * member first; 3 = 3 blocks per SM, largest first; 4 = one single-domain launch per member and
+ * step (no batching); 5 = 128-thread blocks (8 per SM); 6 = 512-thread blocks (2 per SM); 7 =
+ * FP32 members one cell per thread; 8 = FP32 members two cells per thread; 9 = persistent grid
+ * (as many blocks as fit on the GPU at once, each striding over all members' blocks).  Shapes 5..9
+ * need at most 48 members; 7 and 8 apply to FP32 storage only.  The autotuner runs 2 +
+ * trial_steps steps of every available shape on the members (they advance by that many steps per
+ * shape), times each with CUDA events and keeps the fastest.  trial_steps even, >= 2.  choice (may
+ * be NULL) receives the chosen shape, ms_per_step (may be NULL; lbm_batch_shape_count() floats)
+ * the ms per step of every shape, -1 for shapes not available to this batch.  Synchronises the
+ * stream; drops a captured graph. */
 lbm_status lbm_batch_autotune(lbm_batch *b, int trial_steps, int *choice, float *ms_per_step);
+int lbm_batch_shape_count(void);
 
-/* Set / read the launch shape (drops a captured graph). */
+/* Set / read the launch shape (drops a captured graph; LBM_EINVAL for a shape not available). */
 lbm_status lbm_batch_set_shape(lbm_batch *b, int shape);
 int lbm_batch_shape(const lbm_batch *b);
 

@@ -26,10 +26,31 @@
 namespace lbm {
 namespace {
 
-// Launch shapes the autotuner chooses from: resident blocks per SM the batched kernels are compiled
-// for (their register cap), and the slot order of the members in the grid.
-constexpr int kShapes = 4;   // (4 blocks, given order), (3, given), (4, largest first), (3, largest first)
-constexpr int kSequential = kShapes;   // one single-domain launch per member and step
+// Launch shapes the autotuner chooses from (lbm_batch_autotune): threads per block B, resident blocks
+// per SM the batched kernel is compiled for (its register cap), cells per thread of FP32 members
+// (0: each member's own choice, as in its single-domain launch; 1 or 2 for all -- the unrolling of
+// the cell loop), a persistent grid (one set of resident blocks striding over the members' blocks),
+// the slot order (members in the given order or largest first), or one single-domain launch per
+// member and step.
+struct ShapeSpec {
+    int B, minb, cpt;
+    bool persistent, largest_first, sequential;
+};
+constexpr ShapeSpec kShapeSpec[] = {
+    {256, 4, 0, false, false, false},   // 0
+    {256, 3, 0, false, false, false},   // 1
+    {256, 4, 0, false, true, false},    // 2
+    {256, 3, 0, false, true, false},    // 3
+    {256, 4, 0, false, false, true},    // 4: one single-domain launch per member and step
+    {128, 8, 0, false, false, false},   // 5
+    {512, 2, 0, false, false, false},   // 6
+    {256, 4, 1, false, false, false},   // 7: FP32 members one cell per thread
+    {256, 4, 2, false, false, false},   // 8: FP32 members two cells per thread
+    {256, 4, 0, true, false, false},    // 9: persistent grid
+};
+constexpr int kNumShapes = (int)(sizeof(kShapeSpec) / sizeof(kShapeSpec[0]));
+constexpr int kSequential = 4;
+constexpr int kTableShapes = 4;   // shapes 0..3 also run with the member tables in device memory
 
 struct BatchTables {
     const StepArgs *args;     // per member
@@ -37,6 +58,27 @@ struct BatchTables {
     const int *member;        // per slot: member index
     int n;
 };
+
+// FP32 member: two cells per thread?
+template <int S, int CPT> __device__ __forceinline__ bool batch_d32(const StepArgs &a) {
+    return S == LBM_F32 && (CPT == 2 || (CPT == 0 && a.g.N >= kDual32MinCells));
+}
+
+// Block bid of a member's own launch of this step kind (the same block bodies as lbm_step).
+template <int S, bool NEIGHBOR, int B, int CPT>
+__device__ __forceinline__ void batch_block(const StepArgs &a, unsigned bid) {
+    const bool d32 = batch_d32<S, CPT>(a);
+    if constexpr (NEIGHBOR) {
+        if (d32) neighbor_block<S, false, false, true, B>(a, bid, face_blocks_of<B>(a.nface));
+        else neighbor_block<S, false, false, false, B>(a, bid, face_blocks_of<B>(a.nface));
+    } else if constexpr (S == LBM_F32) {
+        if (d32) local_block<S, false, false, true, B>(a, bid);
+        else local_block<S, false, false, false, B>(a, bid);
+    } else {
+        if (a.pack16) local_block<S, false, true, false, B>(a, bid);
+        else local_block<S, false, false, false, B>(a, bid);
+    }
+}
 
 template <int S, bool NEIGHBOR, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_batch_step(BatchTables t) {
@@ -60,18 +102,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_batch_step(BatchTables t) {
         for (int k = threadIdx.x; k < (int)(sizeof(StepArgs) / sizeof(int)); k += kBlock) dst[k] = src[k];
     }
     __syncthreads();
-    // FP32: the member's own choice of cells per thread, as in its single-domain launch
-    const bool d32 = S == LBM_F32 && sa.g.N >= kDual32MinCells;
-    if constexpr (NEIGHBOR) {
-        if (d32) neighbor_block<S, false, false, true>(sa, s_bid, face_blocks_of(sa.nface));
-        else neighbor_block<S, false, false, false>(sa, s_bid, face_blocks_of(sa.nface));
-    } else if constexpr (S == LBM_F32) {
-        if (d32) local_block<S, false, false, true>(sa, s_bid);
-        else local_block<S, false, false, false>(sa, s_bid);
-    } else {
-        if (sa.pack16) local_block<S, false, true>(sa, s_bid);
-        else local_block<S, false, false>(sa, s_bid);
-    }
+    batch_block<S, NEIGHBOR, kBlock, 0>(sa, s_bid);
 }
 
 // Up to kParamMembers members: the step arguments and block tables travel in the kernel's parameter
@@ -85,66 +116,99 @@ struct BatchParams {
 };
 static_assert(sizeof(BatchParams) <= 32000, "kernel parameter space");
 
-template <int S, bool NEIGHBOR, int MINB>
-__global__ void __launch_bounds__(kBlock, MINB) k_batch_step_p(const __grid_constant__ BatchParams p) {
-    int lo = 0, hi = p.n - 1;   // last slot whose first block is <= blockIdx.x (uniform)
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (p.start[mid] <= blockIdx.x) lo = mid;
-        else hi = mid - 1;
-    }
-    const StepArgs &a = p.args[p.member[lo]];
-    const unsigned bid = blockIdx.x - p.start[lo];
-    // FP32: the member's own choice of cells per thread, as in its single-domain launch
-    const bool d32 = S == LBM_F32 && a.g.N >= kDual32MinCells;
-    if constexpr (NEIGHBOR) {
-        if (d32) neighbor_block<S, false, false, true>(a, bid, face_blocks_of(a.nface));
-        else neighbor_block<S, false, false, false>(a, bid, face_blocks_of(a.nface));
-    } else if constexpr (S == LBM_F32) {
-        if (d32) local_block<S, false, false, true>(a, bid);
-        else local_block<S, false, false, false>(a, bid);
-    } else {
-        if (a.pack16) local_block<S, false, true>(a, bid);
-        else local_block<S, false, false>(a, bid);
+template <int S, bool NEIGHBOR, int B, int MINB, int CPT, bool PERSIST>
+__global__ void __launch_bounds__(B, MINB) k_batch_step_p(const __grid_constant__ BatchParams p) {
+    const unsigned total = p.start[p.n];
+    for (unsigned vb = blockIdx.x; vb < total; vb += PERSIST ? gridDim.x : total) {
+        int lo = 0, hi = p.n - 1;   // last slot whose first block is <= vb (uniform)
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.start[mid] <= vb) lo = mid;
+            else hi = mid - 1;
+        }
+        batch_block<S, NEIGHBOR, B, CPT>(p.args[p.member[lo]], vb - p.start[lo]);
     }
 }
 
-// blocks of a member's launch of this kind (the same as its single-domain launch)
-template <int S> unsigned member_blocks(const StepArgs &a, bool neighbor) {
-    const unsigned lb = a.g.N >= kDual32MinCells ? lattice_blocks<S, true>(a.g.N) : lattice_blocks<S, false>(a.g.N);
-    return lb + (neighbor ? face_blocks_of(a.nface) : 0u);
+// blocks of a member's launch of this kind in shape sh (as its single-domain launch for shape 0)
+template <int S> unsigned member_blocks(const StepArgs &a, bool neighbor, int sh) {
+    const ShapeSpec &q = kShapeSpec[sh];
+    const bool d32 = S == LBM_F32 && (q.cpt == 2 || (q.cpt == 0 && a.g.N >= kDual32MinCells));
+    unsigned lb = 0, fb = 0;
+    switch (q.B) {
+        case 128: lb = d32 ? lattice_blocks<S, true, 128>(a.g.N) : lattice_blocks<S, false, 128>(a.g.N);
+                  fb = face_blocks_of<128>(a.nface); break;
+        case 512: lb = d32 ? lattice_blocks<S, true, 512>(a.g.N) : lattice_blocks<S, false, 512>(a.g.N);
+                  fb = face_blocks_of<512>(a.nface); break;
+        default: lb = d32 ? lattice_blocks<S, true, 256>(a.g.N) : lattice_blocks<S, false, 256>(a.g.N);
+                 fb = face_blocks_of<256>(a.nface); break;
+    }
+    return lb + (neighbor ? fb : 0u);
 }
-unsigned member_blocks(int store, const StepArgs &a, bool neighbor) {
+unsigned member_blocks(int store, const StepArgs &a, bool neighbor, int sh) {
     switch (store) {
-        case LBM_F32: return member_blocks<LBM_F32>(a, neighbor);
-        case LBM_F16S: return member_blocks<LBM_F16S>(a, neighbor);
-        default: return member_blocks<LBM_BF16S>(a, neighbor);
+        case LBM_F32: return member_blocks<LBM_F32>(a, neighbor, sh);
+        case LBM_F16S: return member_blocks<LBM_F16S>(a, neighbor, sh);
+        default: return member_blocks<LBM_BF16S>(a, neighbor, sh);
     }
 }
 
-// p: parameter-space tables (null: shared-memory tables t)
-template <int S, int MINB>
-void launch_batch_t(bool neighbor, const BatchTables &t, const BatchParams *p, unsigned blocks, cudaStream_t s) {
-    if (p) {
-        if (neighbor) k_batch_step_p<S, true, MINB><<<blocks, kBlock, 0, s>>>(*p);
-        else k_batch_step_p<S, false, MINB><<<blocks, kBlock, 0, s>>>(*p);
-    } else {
-        if (neighbor) k_batch_step<S, true, MINB><<<blocks, kBlock, 0, s>>>(t);
-        else k_batch_step<S, false, MINB><<<blocks, kBlock, 0, s>>>(t);
+// Resident blocks of a persistent kernel: its occupancy times the SM count (queried once).
+template <class K> unsigned persistent_grid(K kernel, int B) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, B, 0) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (unsigned)(sms * per);
+}
+
+template <int S, bool NEIGHBOR, int B, int MINB, int CPT, bool PERSIST>
+void launch_p(const BatchParams &p, unsigned blocks, cudaStream_t s) {
+    if (PERSIST) {
+        static unsigned grid = 0;   // per kernel (one template instance per kernel)
+        if (!grid) grid = persistent_grid(k_batch_step_p<S, NEIGHBOR, B, MINB, CPT, PERSIST>, B);
+        if (grid && grid < blocks) blocks = grid;
+    }
+    k_batch_step_p<S, NEIGHBOR, B, MINB, CPT, PERSIST><<<blocks, B, 0, s>>>(p);
+}
+template <int S, bool NEIGHBOR>
+void launch_shape(int sh, const BatchTables &t, const BatchParams *p, unsigned blocks, cudaStream_t s) {
+    if (!p) {   // member tables in device memory (more than kParamMembers members): shapes 0..3
+        if (kShapeSpec[sh].minb == 3) k_batch_step<S, NEIGHBOR, 3><<<blocks, kBlock, 0, s>>>(t);
+        else k_batch_step<S, NEIGHBOR, 4><<<blocks, kBlock, 0, s>>>(t);
+        return;
+    }
+    switch (sh) {
+        case 1: case 3: launch_p<S, NEIGHBOR, 256, 3, 0, false>(*p, blocks, s); break;
+        case 5: launch_p<S, NEIGHBOR, 128, 8, 0, false>(*p, blocks, s); break;
+        case 6: launch_p<S, NEIGHBOR, 512, 2, 0, false>(*p, blocks, s); break;
+        case 7: if constexpr (S == LBM_F32) launch_p<S, NEIGHBOR, 256, 4, 1, false>(*p, blocks, s);
+                else launch_p<S, NEIGHBOR, 256, 4, 0, false>(*p, blocks, s);
+                break;
+        case 8: if constexpr (S == LBM_F32) launch_p<S, NEIGHBOR, 256, 4, 2, false>(*p, blocks, s);
+                else launch_p<S, NEIGHBOR, 256, 4, 0, false>(*p, blocks, s);
+                break;
+        case 9: launch_p<S, NEIGHBOR, 256, 4, 0, true>(*p, blocks, s); break;
+        default: launch_p<S, NEIGHBOR, 256, 4, 0, false>(*p, blocks, s); break;
     }
 }
-template <int S>
-void launch_batch_s(int minb, bool neighbor, const BatchTables &t, const BatchParams *p, unsigned blocks,
-                    cudaStream_t s) {
-    if (minb == 3) launch_batch_t<S, 3>(neighbor, t, p, blocks, s);
-    else launch_batch_t<S, 4>(neighbor, t, p, blocks, s);
-}
-void launch_batch(int store, int minb, bool neighbor, const BatchTables &t, const BatchParams *p, unsigned blocks,
+void launch_batch(int store, int sh, bool neighbor, const BatchTables &t, const BatchParams *p, unsigned blocks,
                   cudaStream_t s) {
     switch (store) {
-        case LBM_F32: launch_batch_s<LBM_F32>(minb, neighbor, t, p, blocks, s); break;
-        case LBM_F16S: launch_batch_s<LBM_F16S>(minb, neighbor, t, p, blocks, s); break;
-        default: launch_batch_s<LBM_BF16S>(minb, neighbor, t, p, blocks, s); break;
+        case LBM_F32:
+            if (neighbor) launch_shape<LBM_F32, true>(sh, t, p, blocks, s);
+            else launch_shape<LBM_F32, false>(sh, t, p, blocks, s);
+            break;
+        case LBM_F16S:
+            if (neighbor) launch_shape<LBM_F16S, true>(sh, t, p, blocks, s);
+            else launch_shape<LBM_F16S, false>(sh, t, p, blocks, s);
+            break;
+        default:
+            if (neighbor) launch_shape<LBM_BF16S, true>(sh, t, p, blocks, s);
+            else launch_shape<LBM_BF16S, false>(sh, t, p, blocks, s);
+            break;
     }
 }
 
@@ -176,7 +240,7 @@ struct lbm_batch {
     cudaStream_t stream;
     char *ws;
     BatchLayout L;
-    int shape;                     // 0..kShapes-1, or kSequential
+    int shape;                     // index into kShapeSpec
     unsigned total_nb, total_lc;   // grid sizes of the two step kinds
     BatchParams *params[2];        // parameter-space tables (neighbour, local); null above kParamMembers
     cudaGraphExec_t graph;
@@ -207,15 +271,15 @@ lbm_status batch_upload(lbm_batch *b) {
     const int n = (int)b->dom.size();
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
-    if (b->shape == 2 || b->shape == 3)   // largest member first: its blocks start earliest
+    if (kShapeSpec[b->shape].largest_first)   // largest member first: its blocks start earliest
         std::stable_sort(order.begin(), order.end(),
                          [&](int x, int y) { return b->args[x].g.N > b->args[y].g.N; });
     std::vector<unsigned> snb(n + 1), slc(n + 1);
     snb[0] = slc[0] = 0;
     for (int k = 0; k < n; ++k) {
         const StepArgs &a = b->args[order[k]];
-        snb[k + 1] = snb[k] + member_blocks(b->store, a, true);
-        slc[k + 1] = slc[k] + member_blocks(b->store, a, false);
+        snb[k + 1] = snb[k] + member_blocks(b->store, a, true, b->shape);
+        slc[k + 1] = slc[k] + member_blocks(b->store, a, false, b->shape);
     }
     b->total_nb = snb[n];
     b->total_lc = slc[n];
@@ -254,13 +318,12 @@ void batch_enqueue(lbm_batch *b, int nsteps, int p) {
             for (int m = 0; m < n; ++m) launch_step(b->store, ((p + k) & 1) == 0, false, b->args[m], b->stream);
         return;
     }
-    const int minb = (b->shape == 1 || b->shape == 3) ? 3 : 4;
     for (int k = 0; k < nsteps; ++k) {
         const bool neighbor = ((p + k) & 1) == 0;
         BatchTables t{(const StepArgs *)(b->ws + b->L.args),
                       (const unsigned *)(b->ws + (neighbor ? b->L.start_nb : b->L.start_lc)),
                       (const int *)(b->ws + b->L.member), n};
-        launch_batch(b->store, minb, neighbor, t, b->params[neighbor ? 0 : 1], neighbor ? b->total_nb : b->total_lc,
+        launch_batch(b->store, b->shape, neighbor, t, b->params[neighbor ? 0 : 1], neighbor ? b->total_nb : b->total_lc,
                      b->stream);
     }
 }
@@ -279,6 +342,14 @@ void drop_graph(lbm_batch *b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
     b->graph_steps = 0;
+}
+
+// Shapes 5..9 keep the member tables in the kernel's parameter space only (at most kParamMembers
+// members); FP32 cells-per-thread shapes are the same as shape 0 for 16-bit storage.
+bool shape_available(const lbm_batch *b, int shape) {
+    if (shape >= kTableShapes && shape != kSequential && !b->params[0]) return false;
+    if (b->store != LBM_F32 && kShapeSpec[shape].cpt != 0) return false;
+    return true;
 }
 
 }  // namespace
@@ -405,7 +476,10 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int trial_steps, int *choice, float 
     if (st != LBM_OK) { cudaEventDestroy(e0); return st; }
     float best = 0.0f;
     int best_shape = kSequential;
-    for (int shape = 0; shape <= kSequential && st == LBM_OK; ++shape) {
+    bool any = false;
+    for (int shape = 0; shape < kNumShapes && st == LBM_OK; ++shape) {
+        if (ms_per_step) ms_per_step[shape] = -1.0f;
+        if (!shape_available(b, shape)) continue;
         b->shape = shape;
         st = batch_upload(b);
         if (st != LBM_OK) break;
@@ -422,7 +496,8 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int trial_steps, int *choice, float 
         cudaEventElapsedTime(&ms, e0, e1);
         ms /= (float)trial_steps;
         if (ms_per_step) ms_per_step[shape] = ms;
-        if (shape == 0 || ms < best) { best = ms; best_shape = shape; }
+        if (!any || ms < best) { best = ms; best_shape = shape; }
+        any = true;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -434,13 +509,17 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int trial_steps, int *choice, float 
 
 lbm_status lbm_batch_set_shape(lbm_batch *b, int shape) {
     if (!b) return LBM_EINVAL;
-    if (shape < 0 || shape > kSequential) return bfail(b, LBM_EINVAL, "batch shape out of range");
+    if (shape < 0 || shape >= kNumShapes) return bfail(b, LBM_EINVAL, "batch shape out of range");
+    if (!shape_available(b, shape))
+        return bfail(b, LBM_EINVAL, "batch shape %d needs at most %d members", shape, kParamMembers);
     drop_graph(b);
     b->shape = shape;
     return batch_upload(b);
 }
 
 int lbm_batch_shape(const lbm_batch *b) { return b ? b->shape : -1; }
+
+int lbm_batch_shape_count(void) { return kNumShapes; }
 
 const char *lbm_batch_last_error(const lbm_batch *b) { return b ? b->err : "no batch"; }
 

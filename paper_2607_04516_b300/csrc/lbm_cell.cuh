@@ -1053,12 +1053,13 @@ template <int S, bool D32 = false> __host__ __device__ constexpr int cells_per_t
     return (S == LBM_F32 && !D32) ? 1 : 2;
 }
 
-// lattice blocks of a launch over N cells
-template <int S, bool D32 = false> __host__ __device__ inline unsigned lattice_blocks(long long N) {
+// lattice blocks of a launch over N cells (blocks of B threads)
+template <int S, bool D32 = false, int B = kBlock> __host__ __device__ inline unsigned lattice_blocks(long long N) {
     const long long cpt = cells_per_thread<S, D32>();
-    return (unsigned)(((N + cpt - 1) / cpt + kBlock - 1) / kBlock);
+    return (unsigned)(((N + cpt - 1) / cpt + B - 1) / B);
 }
-__host__ __device__ inline unsigned face_blocks_of(long long nface) { return (unsigned)((nface + kBlock - 1) / kBlock); }
+template <int B = kBlock>
+__host__ __device__ inline unsigned face_blocks_of(long long nface) { return (unsigned)((nface + B - 1) / B); }
 
 // L2 prefetch ahead of the lattice blocks: block b asks the copy engine to bring the population
 // tiles of a block about LBM_PF_BYTES of populations further on into L2 (one bulk prefetch per
@@ -1081,10 +1082,10 @@ __device__ __forceinline__ void prefetch_l2(const char *base, const char *end, c
 
 // The prefetch of lattice block lb + kPfDist (of `nlb`): threads 0..18 take one plane each, the
 // cells of that block shifted by -off[i] in plane opp(i) (neighbour step) or in place (local step).
-template <int S, bool D32, bool NEIGHBOR>
+template <int S, bool D32, bool NEIGHBOR, int B = kBlock>
 __device__ __forceinline__ void prefetch_ahead(const StepArgs &a, unsigned lb, unsigned nlb) {
     constexpr int sb = S == LBM_F32 ? 4 : 2;
-    constexpr long long span = (long long)cells_per_thread<S, D32>() * kBlock;
+    constexpr long long span = (long long)cells_per_thread<S, D32>() * B;
     constexpr unsigned kPfDist = (unsigned)((long long)LBM_PF_BYTES / (span * sb * Q));
     if constexpr (kPfDist == 0) return;
     if (threadIdx.x >= Q || lb + kPfDist >= nlb) return;
@@ -1095,24 +1096,25 @@ __device__ __forceinline__ void prefetch_ahead(const StepArgs &a, unsigned lb, u
     prefetch_l2(base, end, p + c0 * sb, p + (c0 + span) * sb);
 }
 
-template <int S, bool FORCE, bool PACK, bool D32 = false>
+// B: threads per block (the kernels use kBlock; batched launches may choose another size)
+template <int S, bool FORCE, bool PACK, bool D32 = false, int B = kBlock>
 __device__ __forceinline__ void local_block(const StepArgs &a, unsigned bid) {
-    prefetch_ahead<S, D32, false>(a, bid, lattice_blocks<S, D32>(a.g.N));
+    prefetch_ahead<S, D32, false, B>(a, bid, lattice_blocks<S, D32, B>(a.g.N));
     if constexpr (S == LBM_F32 && cells_per_thread<S, D32>() == 2) {
-        const int n0 = (int)(bid * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
+        const int n0 = (int)(bid * 2 * B + threadIdx.x), n1 = n0 + B;
         if (n0 >= a.g.N) return;
         cell2_local_dual_f32<FORCE>(a, n0, n1, true, n1 < a.g.N);
     } else if constexpr (cells_per_thread<S, D32>() == 1) {
-        const int n = (int)(bid * kBlock + threadIdx.x);
+        const int n = (int)(bid * B + threadIdx.x);
         if (n >= a.g.N) return;
         cell_local<S, FORCE>(a, n);
     } else if constexpr (PACK) {
-        const int n0 = (int)(bid * 2 * kBlock + 2 * threadIdx.x);
+        const int n0 = (int)(bid * 2 * B + 2 * threadIdx.x);
         if (n0 >= a.g.N) return;
         if constexpr (kDual16) cellp_local_dual<S, FORCE>(a, n0);
         else cellp_local<S, FORCE>(a, n0);
     } else {
-        const int n0 = (int)(bid * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
+        const int n0 = (int)(bid * 2 * B + threadIdx.x), n1 = n0 + B;
         if (n0 >= a.g.N) return;
         cell2_local<S, FORCE>(a, n0, n1, true, n1 < a.g.N);
     }
@@ -1150,30 +1152,30 @@ __device__ LBM_FACE_INLINE void face_unit(const StepArgs &a, long long t) {
     cell_neighbor_face<S, FORCE>(a, fl, x, y, z);
 }
 
-template <int S, bool FORCE, bool PACK, bool D32 = false>
+template <int S, bool FORCE, bool PACK, bool D32 = false, int B = kBlock>
 __device__ __forceinline__ void neighbor_block(const StepArgs &a, unsigned bid, unsigned face_blocks) {
     if (bid >= face_blocks) {
-        prefetch_ahead<S, D32, true>(a, bid - face_blocks, lattice_blocks<S, D32>(a.g.N));
+        prefetch_ahead<S, D32, true, B>(a, bid - face_blocks, lattice_blocks<S, D32, B>(a.g.N));
         if constexpr (S == LBM_F32 && cells_per_thread<S, D32>() == 2) {
-            const int n0 = (int)((bid - face_blocks) * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
+            const int n0 = (int)((bid - face_blocks) * 2 * B + threadIdx.x), n1 = n0 + B;
             if (n0 >= a.g.N) return;
             cell2_neighbor_interior_dual_f32<FORCE>(a, n0, n1, true, n1 < a.g.N);
         } else if constexpr (cells_per_thread<S, D32>() == 1) {
-            const int n = (int)((bid - face_blocks) * kBlock + threadIdx.x);
+            const int n = (int)((bid - face_blocks) * B + threadIdx.x);
             if (n >= a.g.N) return;
             cell_neighbor_interior<S, FORCE>(a, n);
         } else if constexpr (PACK) {
-            const int n0 = (int)((bid - face_blocks) * 2 * kBlock + 2 * threadIdx.x);
+            const int n0 = (int)((bid - face_blocks) * 2 * B + 2 * threadIdx.x);
             if (n0 >= a.g.N) return;
             cellp_neighbor_interior<S, FORCE>(a, n0);
         } else {
-            const int n0 = (int)((bid - face_blocks) * 2 * kBlock + threadIdx.x), n1 = n0 + kBlock;
+            const int n0 = (int)((bid - face_blocks) * 2 * B + threadIdx.x), n1 = n0 + B;
             if (n0 >= a.g.N) return;
             if constexpr (kDual16) cell2_neighbor_interior_dual<S, FORCE>(a, n0, n1, true, n1 < a.g.N);
             else cell2_neighbor_interior<S, FORCE>(a, n0, n1, true, n1 < a.g.N);
         }
     } else {
-        const long long t = (long long)bid * kBlock + threadIdx.x;
+        const long long t = (long long)bid * B + threadIdx.x;
         if (t >= a.nface) return;
         face_unit<S, FORCE>(a, t);
     }

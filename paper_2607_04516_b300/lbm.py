@@ -89,6 +89,7 @@ SIGNATURES = {
     "lbm_batch_autotune": (_I, [_P, _I, _P, _P]),
     "lbm_batch_set_shape": (_I, [_P, _I]),
     "lbm_batch_shape": (_I, [_P]),
+    "lbm_batch_shape_count": (_I, []),
     "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
     "lbm_batch_destroy": (None, [_P]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
@@ -526,8 +527,10 @@ def lidar_misfit(p, problem: LidarProblem):
     return fn.apply(p, problem)
 
 
-BATCH_SHAPES = ("4 blocks/SM, given order", "3 blocks/SM, given order", "4 blocks/SM, largest first",
-                "3 blocks/SM, largest first", "one launch per member")
+BATCH_SHAPES = ("256 threads, 4 blocks/SM, given order", "256 threads, 3 blocks/SM, given order",
+                "256 threads, 4 blocks/SM, largest first", "256 threads, 3 blocks/SM, largest first",
+                "one launch per member", "128 threads, 8 blocks/SM", "512 threads, 2 blocks/SM",
+                "FP32 one cell per thread", "FP32 two cells per thread", "persistent grid")
 
 
 def _bcheck(status: int, batch=None):
@@ -572,7 +575,7 @@ class Batch:
         _bcheck(load().lbm_batch_launch(self.b), self.b)
 
     def autotune(self, trial_steps: int = 20):
-        """(chosen shape, ms per step of every shape)."""
+        """(chosen shape, ms per step of every shape; -1 where a shape is not available)."""
         choice = ctypes.c_int()
         ms = (ctypes.c_float * len(BATCH_SHAPES))()
         _bcheck(load().lbm_batch_autotune(self.b, int(trial_steps), ctypes.byref(choice), ms), self.b)

@@ -46,6 +46,10 @@ def _state(doms):
 
 # one unit in the last place of the stored value |g| <~ 0.05: FP32, FP16 x 2^14, BF16
 TOL = {"f32": 2e-8, "f16s": 4e-5, "bf16s": 3e-4}
+# shapes 7 and 8 change the FP32 collision form of some members (one cell or two cells per
+# thread: the same arithmetic in another rounding order), a few FP32 ulps per step
+FORCED_CPT = (7, 8)
+TOL_CPT = 2e-7
 
 
 @pytest.mark.parametrize("store", ["f32", "f16s", "bf16s"])
@@ -57,16 +61,22 @@ def test_batched_steps_equal_single_domain_steps(store, nsteps):
     for d in ref:
         d.step(nsteps)
     want = _state(ref)
-    for shape in range(5):
+    assert lbm.load().lbm_batch_shape_count() == len(lbm.BATCH_SHAPES)
+    for shape in range(len(lbm.BATCH_SHAPES)):
         doms = _domains(cases, store)
         b = lbm.Batch(doms)
+        if store != "f32" and shape in FORCED_CPT:
+            with pytest.raises(lbm.LbmError):   # FP32 cells-per-thread shapes only
+                b.shape = shape
+            continue
         b.shape = shape
         b.step(nsteps)
         got = _state(doms)
+        tol = TOL_CPT if shape in FORCED_CPT else TOL[store]
         for g, w, d in zip(got, want, doms):
             assert d.steps_done == nsteps
             diff = float(np.abs(g - w).max())
-            assert diff <= TOL[store], (shape, diff)
+            assert diff <= tol, (shape, diff)
 
 
 def test_graph_replay_equals_direct_steps():
@@ -102,14 +112,16 @@ def test_autotune_picks_a_measured_shape_and_keeps_results():
     b = lbm.Batch(doms)
     choice, ms = b.autotune(trial_steps=4)
     assert 0 <= choice < len(lbm.BATCH_SHAPES) and b.shape == choice
-    assert all(m > 0 for m in ms) and ms[choice] == min(ms)
-    assert all(d.steps_done == 5 * 6 for d in doms)
+    assert len(ms) == len(lbm.BATCH_SHAPES) and all(m > 0 for m in ms)   # FP32, 4 members: all available
+    assert ms[choice] == min(ms)
+    done = len(ms) * 6
+    assert all(d.steps_done == done for d in doms)
     ref = _domains(cases, "f32")
     for d in ref:
-        d.step(30 + 2)
+        d.step(done + 2)
     b.step(2)
     for g, w in zip(_state(doms), _state(ref)):
-        assert float(np.abs(g - w).max()) <= 1e-6   # 32 steps of last-place differences
+        assert float(np.abs(g - w).max()) <= 2e-6   # 62 steps of last-place differences
 
 
 def test_batch_rejects_mixed_members_and_parity():
