@@ -14,9 +14,15 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liblbm.so")
-SOURCES = [os.path.join(CSRC, "lbm_kernels.cu"), os.path.join(CSRC, "lbm_capi.cu"),
-           os.path.join(CSRC, "lbm_noalloc.cu"), os.path.join(CSRC, "lbm_stg.cu"),
-           os.path.join(CSRC, "lbm_adjoint.cu"), os.path.join(CSRC, "lbm_batch.cu")]
+# (source, defines): the step and batched kernels are compiled once per storage type (and forcing),
+# so that their template instantiations build in parallel
+_STORES = ("LBM_F32", "LBM_F16S", "LBM_BF16S")
+UNITS = ([(os.path.join(CSRC, f), ()) for f in ("lbm_kernels.cu", "lbm_capi.cu", "lbm_noalloc.cu", "lbm_stg.cu",
+                                                 "lbm_adjoint.cu", "lbm_batch.cu")]
+         + [(os.path.join(CSRC, "lbm_step_kern.cu"), (f"LBM_INST_S={st}", f"LBM_INST_FORCE={fo}"))
+            for st in _STORES for fo in (0, 1)]
+         + [(os.path.join(CSRC, "lbm_batch_kern.cu"), (f"LBM_INST_S={st}",)) for st in _STORES])
+SOURCES = sorted({src for src, _ in UNITS})
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,7 +41,7 @@ def stale() -> bool:
 def build(force: bool = False, verbose: bool = False, out: str | None = None,
           defines: tuple = ()) -> str:
     """Compile the library (to ``out`` instead of the in-tree path when given, e.g. to compare
-    launch-bound variants passed as ``defines``): one nvcc process per source file in parallel
+    launch-bound variants passed as ``defines``): one nvcc process per compilation unit in parallel
     (objects in a private temporary folder), then one link."""
     import concurrent.futures
     import shutil
@@ -51,16 +57,19 @@ def build(force: bool = False, verbose: bool = False, out: str | None = None,
         flags.insert(0, "-Xptxas=-v")
     objdir = tempfile.mkdtemp(prefix="lbm_build_")
     try:
-        objs = [os.path.join(objdir, os.path.basename(src) + ".o") for src in SOURCES]
+        objs = [os.path.join(objdir, f"{k:02d}_" + os.path.basename(src) + ".o") for k, (src, _) in enumerate(UNITS)]
 
         def compile_one(k):
-            cmd = [nvcc, *flags, "-c", SOURCES[k], "-o", objs[k]]
+            src, unit_defs = UNITS[k]
+            cmd = [nvcc, *flags, *[f"-D{d}" for d in unit_defs], "-c", src, "-o", objs[k]]
             if verbose:
                 print(" ".join(cmd), flush=True)
             subprocess.run(cmd, check=True)
 
-        with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-            list(ex.map(compile_one, range(len(SOURCES))))
+        # longest units first
+        order = sorted(range(len(UNITS)), key=lambda k: "kern" not in UNITS[k][0])
+        with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(UNITS), os.cpu_count() or 4)) as ex:
+            list(ex.map(compile_one, order))
         subprocess.run([nvcc, *ARCH, "-shared", *objs, "-o", tmp], check=True)
     finally:
         shutil.rmtree(objdir, ignore_errors=True)

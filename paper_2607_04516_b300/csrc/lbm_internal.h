@@ -9,10 +9,15 @@ namespace lbm {
 
 constexpr int kRedBlocks = 148 * 8;   // diagnostics pass-1 blocks (8 per SM on a 148-SM B300)
 
+// blocks of a one-thread-per-item launch of 256-thread blocks
+inline unsigned blocks_for(long long n) { return (unsigned)((n + 255) / 256); }
+
 cudaError_t launch_flags(const uint8_t *mask, uint8_t *flags, uint32_t *info, const Geo &G, cudaStream_t s);
 cudaError_t launch_init(int store, const StepArgs &a, const float *rho, const float *u, cudaStream_t s);
 cudaError_t launch_import(int store, const StepArgs &a, const float *g, cudaStream_t s);
 void launch_step(int store, bool neighbor, bool force, const StepArgs &a, cudaStream_t s);
+// The step launch of one storage type and forcing (defined in lbm_step_kern.cu, one object each).
+template <int S, bool FORCE> void launch_step_sf(bool neighbor, const StepArgs &a, cudaStream_t s);
 cudaError_t launch_macros(int store, const StepArgs &a, bool layoutA, float *rho, float *u,
                           cudaStream_t s);
 cudaError_t launch_sample(int store, const StepArgs &a, bool layoutA, const int *ij, int ncol,
