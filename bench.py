@@ -40,7 +40,8 @@ METRIC = "LBM-LES GLUPS & % HBM roofline, FP32 vs 16-bit storage; adjoint/forwar
 STORE_BYTES = {"f32": 4, "f16s": 2, "bf16s": 2}
 DTYPE_NAME = {"f32": "f32", "f16s": "f16-storage/f32-math", "bf16s": "bf16-storage/f32-math"}
 SOURCES = ["paper_2607_04516_b300/csrc/lbm_device.cuh", "paper_2607_04516_b300/csrc/lbm_cell.cuh",
-           "paper_2607_04516_b300/csrc/lbm_kernels.cu"]
+           "paper_2607_04516_b300/csrc/lbm_kernels.cu", "paper_2607_04516_b300/csrc/lbm_step.cuh",
+           "paper_2607_04516_b300/csrc/lbm_step_kern.cu"]
 
 
 def parse():

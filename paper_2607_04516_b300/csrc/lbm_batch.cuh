@@ -56,8 +56,8 @@ template <int S, bool NEIGHBOR, int B, int CPT>
 __device__ __forceinline__ void batch_block(const StepArgs &a, unsigned bid) {
     const bool d32 = batch_d32<S, CPT>(a);
     if constexpr (NEIGHBOR) {
-        if (d32) neighbor_block<S, false, false, true, B>(a, bid, face_blocks_of<B>(a.nface));
-        else neighbor_block<S, false, false, false, B>(a, bid, face_blocks_of<B>(a.nface));
+        if (d32) neighbor_block<S, false, false, true, B, true>(a, bid, face_blocks_of<B>(step_face_cells(a)));
+        else neighbor_block<S, false, false, false, B, true>(a, bid, face_blocks_of<B>(step_face_cells(a)));
     } else if constexpr (S == LBM_F32) {
         if (d32) local_block<S, false, false, true, B>(a, bid);
         else local_block<S, false, false, false, B>(a, bid);
@@ -124,11 +124,11 @@ template <int S> unsigned member_blocks(const StepArgs &a, bool neighbor, int sh
     unsigned lb = 0, fb = 0;
     switch (q.B) {
         case 128: lb = d32 ? lattice_blocks<S, true, 128>(a.g.N) : lattice_blocks<S, false, 128>(a.g.N);
-                  fb = face_blocks_of<128>(a.nface); break;
+                  fb = face_blocks_of<128>(step_face_cells(a)); break;
         case 512: lb = d32 ? lattice_blocks<S, true, 512>(a.g.N) : lattice_blocks<S, false, 512>(a.g.N);
-                  fb = face_blocks_of<512>(a.nface); break;
+                  fb = face_blocks_of<512>(step_face_cells(a)); break;
         default: lb = d32 ? lattice_blocks<S, true, 256>(a.g.N) : lattice_blocks<S, false, 256>(a.g.N);
-                 fb = face_blocks_of<256>(a.nface); break;
+                 fb = face_blocks_of<256>(step_face_cells(a)); break;
     }
     return lb + (neighbor ? fb : 0u);
 }

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_cell.cuh"
 #include "lbm_internal.h"
 #include "lbm_stg.h"
 
@@ -182,6 +183,10 @@ StepArgs args_of(const lbm_domain *d) {
     const long long ix = d->nx > 2 ? d->nx - 2 : 0;
     a.zface_begin = xs * d->ny * d->nz + ys * ix * d->nz;
     a.zfast = zfast_mask(a.g);
+    // (the lattice blocks take the z layers at the speed of interior cells on the two-cell paths:
+    // 16-bit storage, and FP32 lattices of at least kDual32MinCells cells)
+    a.zlat = (zlat_of(a.g) && (d->p.store != LBM_F32 || d->N >= kDual32MinCells)) ? 1 : 0;
+    a.nface_step = a.zlat ? a.zface_begin : a.nface;
     a.pack16 = (d->p.store != LBM_F32 && d->N % 2 == 0 && d->nx % 2 == 0) ? 1 : 0;
     a.ftab = d->L.ngen ? (const uint32_t *)(d->ws + d->L.ftab) : nullptr;
     a.ngen = d->L.ngen;

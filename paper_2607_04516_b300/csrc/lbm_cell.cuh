@@ -50,6 +50,7 @@ LBM_HD void cell_flags(const uint8_t *__restrict__ mask, uint8_t *__restrict__ f
     const bool xy_interior = !lo[0] && !hi[0] && !lo[1] && !hi[1];
     const int zf = zfast_mask(G);
     const bool layer_path = xy_interior && ((lo[2] && (zf & 1)) || (hi[2] && (zf & 2))) && !(lo[2] && hi[2]);
+    if (layer_path && zlat_of(G)) fl |= F_ZL;
     uint32_t nb = 0;
     if (!eq && ((!onface) || layer_path)) {
 #pragma unroll
@@ -779,16 +780,10 @@ LBM_HD void collide2_f32(const StepArgs &a, int n0, int n1, float2 (&g)[Q]) {
     }
 }
 
-template <bool FORCE = false>
-LBM_HD void cell2_local_dual_f32(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
+// The local step's per-cell stores of a collided FP32 pair (solid lanes skipped, store-side
+// bounce-back links, outflow side copies).
+LBM_HD void cell2_local_store_f32(const StepArgs &a, int n0, int n1, uint8_t f0, uint8_t f1, const float2 (&g)[Q]) {
     float *const *P = (float *const *)a.plane;
-    float2 g[Q];   // loaded before the flags are known (n1 may be past N: guard region)
-#pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = make_float2(ld_early_f32(P[i] + n0), ld_early_f32(P[i] + n1));
-    const uint8_t f0 = v0 ? a.flags[n0] : F_SOLID, f1 = v1 ? a.flags[n1] : F_SOLID;
-    if ((f0 & f1) & F_SOLID) return;
-    collide2_f32<FORCE>(a, n0, n1, g);
-    if ((f0 | f1) & F_EQ) eq_lanes<0>(a, n0, n1, f0, f1, g);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         const uint8_t fl = c ? f1 : f0;
@@ -817,18 +812,23 @@ LBM_HD void cell2_local_dual_f32(const StepArgs &a, int n0, int n1, bool v0, boo
 }
 
 template <bool FORCE = false>
-LBM_HD void cell2_neighbor_interior_dual_f32(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
+LBM_HD void cell2_local_dual_f32(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
     float *const *P = (float *const *)a.plane;
-    float2 g[Q];   // loaded before the flags are known (guard region after the planes)
+    float2 g[Q];   // loaded before the flags are known (n1 may be past N: guard region)
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const float *p = P[opp(i)] - a.off[i];
-        g[i] = make_float2(ld_early_f32(p + n0), ld_early_f32(p + n1));
-    }
+    for (int i = 0; i < Q; ++i) g[i] = make_float2(ld_early_f32(P[i] + n0), ld_early_f32(P[i] + n1));
     const uint8_t f0 = v0 ? a.flags[n0] : F_SOLID, f1 = v1 ? a.flags[n1] : F_SOLID;
-    const bool l0 = !(f0 & (F_SOLID | F_FACE)), l1 = !(f1 & (F_SOLID | F_FACE));
-    if (!l0 && !l1) return;
+    if ((f0 & f1) & F_SOLID) return;
     collide2_f32<FORCE>(a, n0, n1, g);
+    if ((f0 | f1) & F_EQ) eq_lanes<0>(a, n0, n1, f0, f1, g);
+    cell2_local_store_f32(a, n0, n1, f0, f1, g);
+}
+
+// The neighbour step's per-cell scatter of a collided FP32 pair (l0 / l1: the lane takes this path;
+// a population heading into a solid goes to the cell's own reversed slot).
+LBM_HD void cell2_neighbor_store_f32(const StepArgs &a, int n0, int n1, bool l0, bool l1, uint8_t f0, uint8_t f1,
+                                     const float2 (&g)[Q]) {
+    float *const *P = (float *const *)a.plane;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         if (!(c ? l1 : l0)) continue;
@@ -848,17 +848,251 @@ LBM_HD void cell2_neighbor_interior_dual_f32(const StepArgs &a, int n0, int n1, 
     }
 }
 
+template <bool FORCE = false>
+LBM_HD void cell2_neighbor_interior_dual_f32(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
+    float *const *P = (float *const *)a.plane;
+    float2 g[Q];   // loaded before the flags are known (guard region after the planes)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float *p = P[opp(i)] - a.off[i];
+        g[i] = make_float2(ld_early_f32(p + n0), ld_early_f32(p + n1));
+    }
+    const uint8_t f0 = v0 ? a.flags[n0] : F_SOLID, f1 = v1 ? a.flags[n1] : F_SOLID;
+    const bool l0 = !(f0 & (F_SOLID | F_FACE)), l1 = !(f1 & (F_SOLID | F_FACE));
+    if (!l0 && !l1) return;
+    collide2_f32<FORCE>(a, n0, n1, g);
+    cell2_neighbor_store_f32(a, n0, n1, l0, l1, f0, f1, g);
+}
+
+// ---------------------------------------------------------------- ground and top layers in the lattice blocks
+// With zlat, a lattice block of the neighbour step whose cells reach into the ground or top layer
+// updates both cells of each thread here: interior cells as cell_neighbor_interior does, F_ZL
+// cells with the rules of cell_neighbor_zlayer (the links crossing a no-slip face bounce back, those
+// crossing a free-slip face reflect specularly within the layer; a solid mirrored source bounces
+// back), both lanes through one paired collision.  The layer of a cell (1: ground, 2: top, 0: other)
+// follows from its index, so every load is issued before the flags are known.
+
+// Storage element that the neighbour step gathers direction i of cell n from (layer zl).
+LBM_HD long long zl_gather_elem(const StepArgs &a, long long n, int zl, int i) {
+    const int cross = cz(i) == 1 ? 1 : (cz(i) == -1 ? 2 : 0);   // the layer whose face the link crosses
+    if (cross != 0 && zl == cross) {
+        if (a.g.face[cross == 1 ? 4 : 5] == LBM_FACE_NOSLIP) return (long long)i * a.g.N + n;
+        const int k = (cx(i) == 0 && cy(i) == 0) ? 0 : dir_c(-cx(i), -cy(i), 0);   // in-layer source
+        const int d = dir_c(cx(i), cy(i), -cz(i));                                  // its direction
+        return (long long)opp(d) * a.g.N + n + a.off[k];
+    }
+    return (long long)opp(i) * a.g.N + n - a.off[i];
+}
+// Storage element that the neighbour step scatters direction j of cell n to (layer zl, solid
+// neighbour mask nb).
+LBM_HD long long zl_scatter_elem(const StepArgs &a, long long n, int zl, unsigned nb, int j) {
+    const int cross = cz(j) == -1 ? 1 : (cz(j) == 1 ? 2 : 0);   // target beyond the ground / top
+    if (cross != 0 && zl == cross) {
+        if (a.g.face[cross == 1 ? 4 : 5] == LBM_FACE_NOSLIP) return (long long)opp(j) * a.g.N + n;
+        const int k = (cx(j) == 0 && cy(j) == 0) ? 0 : dir_c(cx(j), cy(j), 0);   // in-layer consumer
+        const int m = dir_c(cx(j), cy(j), -cz(j));                                // reflected direction
+        const bool bb = k != 0 && ((nb >> k) & 1u);
+        return bb ? (long long)opp(j) * a.g.N + n : (long long)m * a.g.N + n + a.off[k];
+    }
+    return ((nb >> j) & 1u) ? (long long)opp(j) * a.g.N + n : (long long)j * a.g.N + n + a.off[j];
+}
+
+template <int S> LBM_HD float ld_early_dec(const void *base, long long e) {
+    using Cd = Codec<S>;
+    if constexpr (S == LBM_F32) return ld_early_f32((const float *)base + e);
+    else return Cd::dec_bits(ld_early_u16((const unsigned short *)base + e));
+}
+
+// n1 (= n0 + the block size) exists when v1; both cells lie in the same lattice block.
+template <int S, bool FORCE>
+LBM_HD void cell2_neighbor_zl(const StepArgs &a, int n0, int n1, bool v1) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    T *const f = (T *)a.f;
+    const long long A = a.g.sz, N = a.g.N;
+    const int m1 = v1 ? n1 : n0;   // a missing second cell repeats the first, and is discarded
+    const int zl0 = n0 < A ? 1 : (n0 >= N - A ? 2 : 0), zl1 = m1 < A ? 1 : (m1 >= N - A ? 2 : 0);
+    float2 g[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        g[i] = make_float2(ld_early_dec<S>(f, zl_gather_elem(a, n0, zl0, i)), ld_early_dec<S>(f, zl_gather_elem(a, m1, zl1, i)));
+    const uint8_t f0 = a.flags[n0], f1 = v1 ? a.flags[n1] : F_SOLID;
+    const bool l0 = !(f0 & F_SOLID) && (!(f0 & F_FACE) || (f0 & F_ZL));
+    const bool l1 = !(f1 & F_SOLID) && (!(f1 & F_FACE) || (f1 & F_ZL));
+    if (!l0 && !l1) return;
+    const unsigned nb0 = (l0 && (f0 & F_REDIR)) ? a.info[n0] >> 8 : 0u, nb1 = (l1 && (f1 & F_REDIR)) ? a.info[m1] >> 8 : 0u;
+    // a free-slip face whose mirrored source in the layer is solid: bounce-back instead (own slot i)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int zl = c ? zl1 : zl0;
+        const unsigned nb = c ? nb1 : nb0;
+        if (zl == 0 || nb == 0 || a.g.face[zl == 1 ? 4 : 5] != LBM_FACE_FREESLIP) continue;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (cz(i) != (zl == 1 ? 1 : -1) || (cx(i) == 0 && cy(i) == 0)) continue;
+            if ((nb >> dir_c(-cx(i), -cy(i), 0)) & 1u) (c ? g[i].y : g[i].x) = Cd::dec(f[(long long)i * N + (c ? m1 : n0)]);
+        }
+    }
+    if constexpr (FORCE) {
+        const float2 drho = collide2_forced<0>(g, a);
+        nudge2(a, n0, m1, drho, g);
+    } else {
+        collide2<0>(g, a);
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!(c ? l1 : l0)) continue;
+        const int n = c ? n1 : n0, zl = c ? zl1 : zl0;
+        const unsigned nb = c ? nb1 : nb0;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) f[zl_scatter_elem(a, n, zl, nb, j)] = Cd::enc(c ? g[j].y : g[j].x);
+    }
+}
+
+// Lattice blocks that lie wholly in the ground layer or wholly in the top layer (zlat) take the
+// interior two-cell path with the rules of the crossing links fixed at compile time (ZK below): the
+// gather of such a link reads the cell's own slot (no-slip: bounce-back) or the mirrored
+// population of the in-layer source (free-slip), and its scatter writes the cell's own reversed
+// slot or the mirrored slot of the in-layer consumer.  No tables and no per-lane selection, so
+// these cells cost what interior cells cost.  Cells with solid neighbours on a free-slip layer
+// (whose mirrored source may be solid) and blocks that straddle a layer boundary take
+// cell2_neighbor_zl.
+enum : int { ZK_INTERIOR = 0, ZK_GROUND_NOSLIP = 1, ZK_GROUND_FREESLIP = 2, ZK_TOP_NOSLIP = 3, ZK_TOP_FREESLIP = 4,
+             ZK_MIXED = 5 };
+__host__ __device__ constexpr bool zk_ground(int zk) { return zk == ZK_GROUND_NOSLIP || zk == ZK_GROUND_FREESLIP; }
+__host__ __device__ constexpr bool zk_noslip(int zk) { return zk == ZK_GROUND_NOSLIP || zk == ZK_TOP_NOSLIP; }
+// the gather of direction i crosses the layer's face
+__host__ __device__ constexpr bool zk_cross_in(int zk, int i) { return zk_ground(zk) ? cz(i) == 1 : cz(i) == -1; }
+// the scatter of direction j crosses the layer's face
+__host__ __device__ constexpr bool zk_cross_out(int zk, int j) { return zk_ground(zk) ? cz(j) == -1 : cz(j) == 1; }
+
+// Base of the gather of direction i (element at base + cell), and of the scatter of direction j.
+template <class T, int ZK>
+LBM_HD T *zk_gather_base(const StepArgs &a, int i) {
+    T *const *P = (T *const *)a.plane;
+    if (ZK != ZK_INTERIOR && zk_cross_in(ZK, i)) {
+        if (zk_noslip(ZK)) return P[i];
+        const int kk = (cx(i) == 0 && cy(i) == 0) ? 0 : dir_c(-cx(i), -cy(i), 0);   // in-layer source
+        return P[opp(dir_c(cx(i), cy(i), -cz(i)))] + a.off[kk];
+    }
+    return P[opp(i)] - a.off[i];
+}
+template <class T, int ZK>
+LBM_HD T *zk_scatter_base(const StepArgs &a, int j) {
+    T *const *P = (T *const *)a.plane;
+    if (ZK != ZK_INTERIOR && zk_cross_out(ZK, j)) {
+        if (zk_noslip(ZK)) return P[opp(j)];
+        const int kk = (cx(j) == 0 && cy(j) == 0) ? 0 : dir_c(cx(j), cy(j), 0);     // in-layer consumer
+        return P[dir_c(cx(j), cy(j), -cz(j))] + a.off[kk];
+    }
+    return P[j] + a.off[j];
+}
+
+template <int S, bool FORCE> LBM_COLD_HD void neighbor_zl_cells(const StepArgs &a, int n0, int n1, bool v1);
+
+// 16-bit storage, cells n0 and n0 + D of a ground or top block.
+template <int S, bool FORCE, int ZK, int D>
+LBM_HD void cell2_neighbor_layer_dual(const StepArgs &a, int n0, bool v1) {
+    using T = unsigned short;
+    const int n1 = n0 + D;
+    uint32_t pk[Q];   // loaded before the flags are known (guard region after the planes)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T *p = zk_gather_base<T, ZK>(a, i);
+        pk[i] = ld_early_u16(p + n0) | (ld_early_u16(p + n1) << 16);
+    }
+    const uint8_t f0 = a.flags[n0], f1 = v1 ? a.flags[n1] : F_SOLID;
+    const bool l0 = !(f0 & F_SOLID) && (!(f0 & F_FACE) || (f0 & F_ZL));
+    const bool l1 = !(f1 & F_SOLID) && (!(f1 & F_FACE) || (f1 & F_ZL));
+    if (!l0 && !l1) return;
+    if (!zk_noslip(ZK) && ((f0 | f1) & F_REDIR)) {   // a mirrored source may be solid
+        neighbor_zl_cells<S, FORCE>(a, n0, n1, v1);
+        return;
+    }
+    if constexpr (FORCE) collide2_packed_forced<S>(a, n0, n1, 0, 0, pk);
+    else collide2_packed<S>(pk, a);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!(c ? l1 : l0)) continue;
+        const int n = c ? n1 : n0;
+        const unsigned nb = ((c ? f1 : f0) & F_REDIR) ? a.info[n] >> 8 : 0u;   // (no-slip layer: no crossing bits)
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const T v = (T)(c ? pk[j] >> 16 : pk[j] & 0xffffu);
+            if (!zk_cross_out(ZK, j) && ((nb >> j) & 1u)) ((T *const *)a.plane)[opp(j)][n] = v;
+            else zk_scatter_base<T, ZK>(a, j)[n] = v;
+        }
+    }
+}
+
+// FP32 storage, cells n0 and n0 + D of a ground or top block.
+template <bool FORCE, int ZK, int D>
+LBM_HD void cell2_neighbor_layer_dual_f32(const StepArgs &a, int n0, bool v1) {
+    const int n1 = n0 + D;
+    float2 g[Q];   // loaded before the flags are known (guard region after the planes)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float *p = zk_gather_base<float, ZK>(a, i);
+        g[i] = make_float2(ld_early_f32(p + n0), ld_early_f32(p + n1));
+    }
+    const uint8_t f0 = a.flags[n0], f1 = v1 ? a.flags[n1] : F_SOLID;
+    const bool l0 = !(f0 & F_SOLID) && (!(f0 & F_FACE) || (f0 & F_ZL));
+    const bool l1 = !(f1 & F_SOLID) && (!(f1 & F_FACE) || (f1 & F_ZL));
+    if (!l0 && !l1) return;
+    if (!zk_noslip(ZK) && ((f0 | f1) & F_REDIR)) {   // a mirrored source may be solid
+        neighbor_zl_cells<LBM_F32, FORCE>(a, n0, n1, v1);
+        return;
+    }
+    collide2_f32<FORCE>(a, n0, n1, g);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!(c ? l1 : l0)) continue;
+        const int n = c ? n1 : n0;
+        const unsigned nb = ((c ? f1 : f0) & F_REDIR) ? a.info[n] >> 8 : 0u;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const float v = c ? g[j].y : g[j].x;
+            if (!zk_cross_out(ZK, j) && ((nb >> j) & 1u)) ((float *const *)a.plane)[opp(j)][n] = v;
+            else zk_scatter_base<float, ZK>(a, j)[n] = v;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- post-collision readback
+// Layout A, a cell on a face layer: each population from the first location its scatter wrote.
+// A called function, so that the general resolution's registers do not weigh on the callers'
+// common paths (the diagnostics kernel reads every cell through read_post).
+template <int S>
+LBM_COLD_HD void read_post_face(const StepArgs &a, long long n, float (&g)[Q]) {
+    using Cd = Codec<S>;
+    using T = typename Cd::T;
+    const T *f = (const T *)a.f;
+    int x, y, z;
+    cell_coords(a.g, n, x, y, z);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        float v = NAN;   // stays NaN only if no location held it (cannot happen for fluid cells)
+        bool found = false;
+        scatter_targets(a.g, a.flags, x, y, z, j, true, [&](int kind, long long idx) {
+            if (found) return;
+            const T *base = kind == 0 ? f : (const T *)a.side[kind - 1];
+            v = Cd::dec(base[idx]);
+            found = true;
+        });
+        g[j] = v;
+    }
+}
+
 // Shifted post-collision populations of a non-solid cell n in the current layout.
 template <int S>
 LBM_HD void read_post(const StepArgs &a, long long n, uint8_t fl, bool layoutA, float (&g)[Q]) {
     using Cd = Codec<S>;
     using T = typename Cd::T;
     const T *f = (const T *)a.f;
-    int x, y, z;
-    cell_coords(a.g, n, x, y, z);
     if (fl & F_EQ) {
         // the equilibrium populations as stored (and as consumed by the neighbours)
+        int x, y, z;
+        cell_coords(a.g, n, x, y, z);
         float ux, uy, uz;
         eq_velocity(a, x, y, z, ux, uy, uz);
         equilibrium_shifted(a.rho_b - 1.0f, ux, uy, uz, g);
@@ -881,18 +1115,7 @@ LBM_HD void read_post(const StepArgs &a, long long n, uint8_t fl, bool layoutA, 
             g[j] = Cd::dec(f[((nb >> j) & 1u) ? (long long)opp(j) * a.g.N + n : (long long)j * a.g.N + n + a.off[j]]);
         return;
     }
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-        float v = NAN;   // stays NaN only if no location held it (cannot happen for fluid cells)
-        bool found = false;
-        scatter_targets(a.g, a.flags, x, y, z, j, true, [&](int kind, long long idx) {
-            if (found) return;
-            const T *base = kind == 0 ? f : (const T *)a.side[kind - 1];
-            v = Cd::dec(base[idx]);
-            found = true;
-        });
-        g[j] = v;
-    }
+    read_post_face<S>(a, n, g);
 }
 
 LBM_HD void macros_of(const StepArgs &a, const float (&g)[Q], float &rho, float &ux, float &uy,
@@ -987,6 +1210,14 @@ LBM_HD void diag_cell(const StepArgs &a, long long n, bool layoutA, DiagAcc &acc
         if ((f1 == LBM_FACE_INFLOW_EQ || f1 == LBM_FACE_OUTFLOW_ZG) && p[ax] == dim(a.g, ax) - 1)
             acc.flux += (double)r * uu[ax];
     }
+}
+
+// Face cell t of the face enumeration (face_cell_xyz).
+template <int S>
+LBM_HD void diag_face_cell(const StepArgs &a, long long t, bool layoutA, DiagAcc &acc) {
+    int x, y, z;
+    face_cell_xyz(a.g, t, x, y, z);
+    diag_cell<S>(a, cell_of(a.g, x, y, z), layoutA, acc);
 }
 
 // Fold the threads' diagnostics of one block (blockDim.x == B) into part[0..3] = (mass, net
@@ -1152,10 +1383,127 @@ __device__ LBM_FACE_INLINE void face_unit(const StepArgs &a, long long t) {
     cell_neighbor_face<S, FORCE>(a, fl, x, y, z);
 }
 
-template <int S, bool FORCE, bool PACK, bool D32 = false, int B = kBlock>
-__device__ __forceinline__ void neighbor_block(const StepArgs &a, unsigned bid, unsigned face_blocks) {
-    if (bid >= face_blocks) {
+// A lattice block lb of the neighbour step whose cells reach into the ground or top layer (zlat),
+// of kind zk (block_layer_kind): the static layer path on two cells per thread, else (a block
+// straddling a layer boundary, or one cell per thread) cell2_neighbor_zl.  The single-domain step
+// runs these blocks in a kernel of their own (k_step_layers), so that their five variants do not
+// weigh on the registers of the main kernel; the batched kernels take them inline.
+// the per-cell layer form for the few blocks that straddle a layer boundary (a called function:
+// its registers stay apart from the kernel's)
+template <int S, bool FORCE>
+LBM_COLD_HD void neighbor_zl_cells(const StepArgs &a, int n0, int n1, bool v1) {
+    cell2_neighbor_zl<S, FORCE>(a, n0, n1, v1);
+}
+
+template <int S, bool FORCE, bool D32, int B>
+LBM_HD void neighbor_layer_unit(const StepArgs &a, unsigned lb, int zk, unsigned tid) {
+    constexpr long long cpt = cells_per_thread<S, D32>();
+    const long long n0 = (long long)lb * cpt * B + tid, n1 = n0 + B;
+    if (n0 >= a.g.N) return;
+    const bool v1 = cpt == 2 && n1 < a.g.N;
+    if constexpr (cpt == 2) {
+#define LBM_LAYER_CASE(ZKV)                                                                                    \
+        case ZKV:                                                                                              \
+            if constexpr (S == LBM_F32) cell2_neighbor_layer_dual_f32<FORCE, ZKV, B>(a, (int)n0, v1);          \
+            else cell2_neighbor_layer_dual<S, FORCE, ZKV, B>(a, (int)n0, v1);                                  \
+            return;
+        switch (zk) {
+            LBM_LAYER_CASE(ZK_GROUND_NOSLIP)
+            LBM_LAYER_CASE(ZK_GROUND_FREESLIP)
+            LBM_LAYER_CASE(ZK_TOP_NOSLIP)
+            LBM_LAYER_CASE(ZK_TOP_FREESLIP)
+            default: break;
+        }
+#undef LBM_LAYER_CASE
+    }
+    neighbor_zl_cells<S, FORCE>(a, (int)n0, (int)n1, v1);
+}
+
+// The lattice blocks of the neighbour step take the ground and top layers (zlat): 1, or 0 to leave
+// them to the face blocks.
+#ifndef LBM_ZLAT
+#define LBM_ZLAT 1
+#endif
+// face cells the neighbour step's face blocks update
+__host__ __device__ inline long long step_face_cells(const StepArgs &a) { return LBM_ZLAT ? a.nface_step : a.nface; }
+
+// Lattice blocks (of span cells, nlb in all) that the single-domain neighbour step gives to
+// k_step_layers: [0, g1) and [t0, nlb), the blocks that reach into the ground or top layer; the
+// main kernel takes [g1, t0).  Without zlat: none (g1 = 0, t0 = nlb).
+struct LayerSplit {
+    unsigned g1, t0;
+};
+__host__ __device__ inline LayerSplit layer_split(const StepArgs &a, long long span, unsigned nlb) {
+    if (!LBM_ZLAT || !a.zlat) return {0u, nlb};
+    const long long A = a.g.sz;
+    long long g1 = (A + span - 1) / span, t0 = (a.g.N - A) / span;
+    if (g1 > (long long)nlb) g1 = nlb;
+    if (t0 < g1) t0 = g1 = nlb;   // the layers reach every block: all in k_step_layers
+    return {(unsigned)g1, (unsigned)t0};
+}
+
+// Kind of the lattice block lb (of span cells) with respect to the z layers (zlat).
+LBM_HD int block_layer_kind(const StepArgs &a, unsigned lb, long long span) {
+    const long long A = a.g.sz, c0 = (long long)lb * span;
+    const long long c1 = c0 + span < a.g.N ? c0 + span : a.g.N;
+    if (c0 >= A && c1 <= a.g.N - A) return ZK_INTERIOR;
+    if (c1 <= A) return a.g.face[4] == LBM_FACE_NOSLIP ? ZK_GROUND_NOSLIP : ZK_GROUND_FREESLIP;
+    if (c0 >= a.g.N - A) return a.g.face[5] == LBM_FACE_NOSLIP ? ZK_TOP_NOSLIP : ZK_TOP_FREESLIP;
+    return ZK_MIXED;
+}
+
+// Position of the face blocks in the grid of a neighbour step.  The face blocks are latency-bound
+// (table lookups, one cell per thread) and the lattice blocks bandwidth-bound; launched all first,
+// the face blocks filled the GPU for their first waves with the DRAM half idle (about 55 us per
+// step on the 400 x 400 x 80 city, for 16-bit and FP32 storage alike).  With pshift >= 0 the face
+// blocks sit at every 2^pshift-th unit instead (from unit 0, while they last) and the lattice
+// blocks fill the units between, in order, so that the face cells' latency hides under the lattice
+// traffic.  pshift < 0: face blocks first.
+#ifndef LBM_FACE_INTERLEAVE
+#define LBM_FACE_INTERLEAVE 1
+#endif
+// shift of the face-block period for fb face blocks among units units (-1: face blocks first)
+__host__ __device__ inline int face_period_shift(unsigned fb, unsigned units) {
+    if (!LBM_FACE_INTERLEAVE || fb == 0) return -1;
+    int s = 0;
+    while ((2ull << s) * fb <= units) ++s;   // the largest power of two with 2^s fb <= units
+    return s;
+}
+// unit u -> face block (*face = true) or lattice block, its index in its kind
+__device__ __forceinline__ unsigned unit_of(unsigned u, unsigned fb, int pshift, bool &face) {
+    if (pshift < 0) {
+        face = u < fb;
+        return face ? u : u - fb;
+    }
+    const unsigned q = u >> pshift;
+    const bool at = (u & ((1u << pshift) - 1u)) == 0u;
+    face = at && q < fb;
+    if (face) return q;
+    const unsigned before = q + (at ? 0u : 1u);   // face units at positions below u
+    return u - (before < fb ? before : fb);
+}
+
+// unit: this block's place in the launch; the lattice blocks of the launch start at lattice block
+// lb0.  LAYERS: the launch also covers the ground and top blocks (zlat), handled through
+// neighbor_layer_unit, inline (the single-domain step gives them to k_step_layers instead).
+template <int S, bool FORCE, bool PACK, bool D32 = false, int B = kBlock, bool LAYERS = false>
+__device__ __forceinline__ void neighbor_block(const StepArgs &a, unsigned unit, unsigned face_blocks, int pshift = -1,
+                                               unsigned lb0 = 0) {
+    bool face;
+    const unsigned ub = unit_of(unit, face_blocks, pshift, face);
+    // below, bid - face_blocks is the lattice block, bid the face block
+    const unsigned bid = face ? ub : ub + face_blocks + lb0;
+    if (!face) {
         prefetch_ahead<S, D32, true, B>(a, bid - face_blocks, lattice_blocks<S, D32, B>(a.g.N));
+        if constexpr (LAYERS) {
+            if (LBM_ZLAT && a.zlat) {
+                const int zk = block_layer_kind(a, bid - face_blocks, (long long)cells_per_thread<S, D32>() * B);
+                if (zk != ZK_INTERIOR) {
+                    neighbor_layer_unit<S, FORCE, D32, B>(a, bid - face_blocks, zk, threadIdx.x);
+                    return;
+                }
+            }
+        }
         if constexpr (S == LBM_F32 && cells_per_thread<S, D32>() == 2) {
             const int n0 = (int)((bid - face_blocks) * 2 * B + threadIdx.x), n1 = n0 + B;
             if (n0 >= a.g.N) return;
@@ -1176,7 +1524,7 @@ __device__ __forceinline__ void neighbor_block(const StepArgs &a, unsigned bid, 
         }
     } else {
         const long long t = (long long)bid * B + threadIdx.x;
-        if (t >= a.nface) return;
+        if (t >= step_face_cells(a)) return;
         face_unit<S, FORCE>(a, t);
     }
 }

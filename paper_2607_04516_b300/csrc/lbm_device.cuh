@@ -38,6 +38,14 @@
 // every helper is usable from host code too, so the per-cell update can be exercised off-GPU
 #define LBM_HD __host__ __device__ __forceinline__
 
+// a rarely taken path kept out of line on the device (LBM_COLD_HD: callable from host builds too)
+#ifdef __CUDA_ARCH__
+#define LBM_COLD __noinline__
+#else
+#define LBM_COLD
+#endif
+#define LBM_COLD_HD __host__ __device__ __noinline__
+
 namespace lbm {
 
 constexpr int Q = 19;
@@ -62,10 +70,27 @@ __host__ __device__ constexpr float wgt(int i) {
     return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
 }
 __host__ __device__ constexpr int cc(int i, int a) { return a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i)); }
-// direction index of velocity (vx, vy, vz), compile-time (-1 if not a D3Q19 velocity)
-__host__ __device__ constexpr int dir_c(int vx, int vy, int vz, int i = 0) {
-    return i == Q ? -1 : ((cx(i) == vx && cy(i) == vy && cz(i) == vz) ? i : dir_c(vx, vy, vz, i + 1));
+// direction index of velocity (vx, vy, vz), -1 if not a D3Q19 velocity (a flat switch, so that the
+// compiler folds it wherever the velocity is a constant, e.g. in unrolled direction loops)
+__host__ __device__ constexpr int dir_c(int vx, int vy, int vz) {
+    switch ((vx + 1) * 9 + (vy + 1) * 3 + (vz + 1)) {
+        case 13: return 0;                        // (0, 0, 0)
+        case 22: return 1;  case 4: return 2;     // (+1, 0, 0) (-1, 0, 0)
+        case 16: return 3;  case 10: return 4;    // (0, +1, 0) (0, -1, 0)
+        case 14: return 5;  case 12: return 6;    // (0, 0, +1) (0, 0, -1)
+        case 25: return 7;  case 1: return 8;     // (+1, +1, 0) (-1, -1, 0)
+        case 23: return 9;  case 3: return 10;    // (+1, 0, +1) (-1, 0, -1)
+        case 17: return 11; case 9: return 12;    // (0, +1, +1) (0, -1, -1)
+        case 19: return 13; case 7: return 14;    // (+1, -1, 0) (-1, +1, 0)
+        case 21: return 15; case 5: return 16;    // (+1, 0, -1) (-1, 0, +1)
+        case 15: return 17; case 11: return 18;   // (0, +1, -1) (0, -1, +1)
+        default: return -1;
+    }
 }
+constexpr bool dir_c_consistent(int i = 0) {
+    return i == Q || (dir_c(cx(i), cy(i), cz(i)) == i && dir_c_consistent(i + 1));
+}
+static_assert(dir_c_consistent(), "dir_c must invert (cx, cy, cz)");
 
 // Runtime (non-constant) direction arithmetic from packed constants.  Component a of c_d is
 // ((PACK_a >> 2d) & 3) - 1; DIR_k holds, in 5-bit fields, the direction index of the velocity with
@@ -92,7 +117,9 @@ enum : uint8_t {
     F_EQ = 2,      // equilibrium boundary cell (on an INFLOW_EQ face layer)
     F_FACE = 4,    // on a face layer: the neighbour step handles it in the face blocks
     F_ZG = 8,      // on an outflow face layer: also stores its inward populations to the side buffer
-    F_REDIR = 16   // has a solid neighbour and stores bounce-back links into it (see cell_local)
+    F_REDIR = 16,  // has a solid neighbour and stores bounce-back links into it (see cell_local)
+    F_ZL = 32      // ground / top layer cell (interior x and y) that the neighbour step updates in the
+                   // lattice blocks instead of the face blocks (both z faces no-slip or free-slip)
 };
 
 // ---------------------------------------------------------------- storage codecs
@@ -212,6 +239,9 @@ struct StepArgs {
     int zwrap;                  // nz * sz: cell offset of a periodic wrap along z
     long long zface_begin;      // first face-enumeration index of the z faces (interior x, y)
     int zfast;                  // bit 0 / bit 1: the z- / z+ face cells take the layer path
+    int zlat;                   // both z faces take the layer path, in the lattice blocks (F_ZL cells)
+    long long nface_step;       // face cells the neighbour step's face blocks update: nface, or
+                                // zface_begin when the lattice blocks take the z layers (zlat)
     int pack16;                 // 16-bit storage with N and nx even: lattice blocks update pairs of
                                 // adjacent cells with 4-byte accesses
     const float4 *ueq[6];       // synthetic inflow turbulence (App. F): per inflow face x-, x+, y-,
@@ -262,6 +292,10 @@ LBM_HD int zfast_mask(const Geo &G) {
     const auto ok = [](int k) { return k == LBM_FACE_NOSLIP || k == LBM_FACE_FREESLIP; };
     return (ok(G.face[4]) ? 1 : 0) | (ok(G.face[5]) ? 2 : 0);
 }
+// The lattice blocks of the neighbour step take the ground and top layers (interior x and y) when
+// both z faces take the layer path: then the face enumeration's z part is not visited by the face
+// blocks, and those cells carry F_ZL.
+LBM_HD bool zlat_of(const Geo &G) { return zfast_mask(G) == 3; }
 
 // ---------------------------------------------------------------- special functions
 // 1/x and square roots of the one-cell collision through the GPU's special-function unit
@@ -282,6 +316,38 @@ LBM_HD float sqrt_pos_fast(float x) {   // x > 0
 #endif
 }
 LBM_HD float sqrt_nonneg_fast(float x) { return x > 0.0f ? sqrt_pos_fast(x) : 0.0f; }
+
+// Reciprocals and square roots of the pair collisions.  FAST = true: single special-function-unit
+// instructions (rcp.approx / sqrt.approx, relative error ~2^-22, far below the FP32 rounding a step
+// accumulates anyway) with no slow-path branch -- the FP32-storage pair collision (collide2), whose
+// kernels run at 3 blocks per SM; FAST = false: the IEEE forms -- the 16-bit pair collision, where at
+// 4 blocks per SM the branch-free forms made the compiler spill (measured slower on B300).  Host
+// builds take the exact forms.  LBM_FAST2 = 0 / 1 forces one form everywhere (for measurements).
+#ifndef LBM_FAST2
+#define LBM_FAST2 -1
+#endif
+template <bool FAST> LBM_HD float rcp2_lane(float x) {
+#ifdef __CUDA_ARCH__
+    if ((LBM_FAST2 < 0 && FAST) || LBM_FAST2 == 1) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+#endif
+    return 1.0f / x;
+}
+template <bool FAST> LBM_HD float sqrt2_lane(float x) {   // x >= 0
+#ifdef __CUDA_ARCH__
+    if ((LBM_FAST2 < 0 && FAST) || LBM_FAST2 == 1) {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+#endif
+    return sqrtf(x);
+}
+template <bool FAST> LBM_HD float2 rcp2(float2 x) { return make_float2(rcp2_lane<FAST>(x.x), rcp2_lane<FAST>(x.y)); }
+template <bool FAST> LBM_HD float2 sqrt2(float2 x) { return make_float2(sqrt2_lane<FAST>(x.x), sqrt2_lane<FAST>(x.y)); }
 
 // ---------------------------------------------------------------- physics (FP32)
 // Equilibrium in shifted form: g^eq_i = f^eq_i - w_i = w_i (drho + rho (3 c.u + 4.5 (c.u)^2
@@ -443,6 +509,11 @@ LBM_HD float2 fma2(float2 a, float2 b, float2 c) {
 }
 LBM_HD float2 sub2(float2 a, float2 b) { return fma2(b, v2(-1.0f), a); }   // a - b, exact rounding
 LBM_HD float2 fms2(float2 a, float2 b, float2 c) { return fma2(make_float2(-a.x, -a.y), b, c); }   // c - a b
+// 2 / x (the relaxation rate from tau + sqrt(...)): one rounded division in the IEEE form
+template <bool FAST> LBM_HD float2 two_over2(float2 x) {
+    if ((LBM_FAST2 < 0 && FAST) || LBM_FAST2 == 1) return mul2(v2(2.0f), rcp2<FAST>(x));
+    return make_float2(2.0f / x.x, 2.0f / x.y);
+}
 
 // The two-cell collision in two phases over an accessor get(i) -> float2 (the shifted populations
 // of direction i, scaled by 2^LOG2S) and put(i, float2), for callers short of registers: the
@@ -506,9 +577,7 @@ LBM_HD Relax2 collide2_moments(Get get, const StepArgs &a) {
     const float2 drho = LOG2S ? mul2(v2(iS), m0) : m0;
     const float2 rho = add2(v2(1.0f), drho);
     Relax2 r;
-    // IEEE division and square roots here (measured faster than the special-function forms when
-    // both lanes go through them together)
-    const float2 irho = make_float2(1.0f / rho.x, 1.0f / rho.y);
+    const float2 irho = rcp2<false>(rho);
     const float2 irs = LOG2S ? mul2(v2(iS), irho) : irho;
     r.ux = mul2(jx, irs); r.uy = mul2(jy, irs); r.uz = mul2(jz, irs);
     const float2 d3r = mul2(m0, v2(1.0f / 3.0f));
@@ -518,8 +587,8 @@ LBM_HD Relax2 collide2_moments(Get get, const StepArgs &a) {
     const float2 pd = fma2(pzz, pzz, fma2(pyy, pyy, mul2(pxx, pxx)));
     const float2 po = fma2(pyz, pyz, fma2(pxz, pxz, mul2(pxy, pxy)));
     const float2 pp2 = fma2(v2(4.0f), po, mul2(v2(2.0f), pd));   // 2 Pi:Pi (times S^2)
-    const float2 arg = fma2(mul2(v2(a.c2x18 * iS), irho), make_float2(sqrtf(pp2.x), sqrtf(pp2.y)), v2(a.tau * a.tau));
-    const float2 om = make_float2(2.0f / (a.tau + sqrtf(arg.x)), 2.0f / (a.tau + sqrtf(arg.y)));
+    const float2 arg = fma2(mul2(v2(a.c2x18 * iS), irho), sqrt2<false>(pp2), v2(a.tau * a.tau));
+    const float2 om = two_over2<false>(add2(v2(a.tau), sqrt2<false>(arg)));
     const float2 uu = fma2(r.uz, r.uz, fma2(r.uy, r.uy, mul2(r.ux, r.ux)));
     const float2 e = fms2(mul2(v2(1.5f), rho), uu, drho);
     if (LBM_RELAX_FOLD) {
@@ -616,9 +685,7 @@ LBM_HD void collide2(float2 (&g)[Q], const StepArgs &a) {
     const float2 sxy = sub2(s7, s13), sxz = sub2(s9, s15), syz = sub2(s11, s17);
     const float2 drho = LOG2S ? mul2(v2(iS), m0) : m0;
     const float2 rho = add2(v2(1.0f), drho);
-    // IEEE division and square roots here (measured faster than the special-function forms when
-    // both lanes go through them together)
-    const float2 irho = make_float2(1.0f / rho.x, 1.0f / rho.y);
+    const float2 irho = rcp2<true>(rho);
     const float2 irs = LOG2S ? mul2(v2(iS), irho) : irho;
     const float2 ux = mul2(jx, irs), uy = mul2(jy, irs), uz = mul2(jz, irs);
     const float2 d3r = mul2(m0, v2(1.0f / 3.0f));
@@ -628,8 +695,8 @@ LBM_HD void collide2(float2 (&g)[Q], const StepArgs &a) {
     const float2 pd = fma2(pzz, pzz, fma2(pyy, pyy, mul2(pxx, pxx)));
     const float2 po = fma2(pyz, pyz, fma2(pxz, pxz, mul2(pxy, pxy)));
     const float2 pp2 = fma2(v2(4.0f), po, mul2(v2(2.0f), pd));   // 2 Pi:Pi (times S^2)
-    const float2 arg = fma2(mul2(v2(a.c2x18 * iS), irho), make_float2(sqrtf(pp2.x), sqrtf(pp2.y)), v2(a.tau * a.tau));
-    const float2 om = make_float2(2.0f / (a.tau + sqrtf(arg.x)), 2.0f / (a.tau + sqrtf(arg.y)));
+    const float2 arg = fma2(mul2(v2(a.c2x18 * iS), irho), sqrt2<true>(pp2), v2(a.tau * a.tau));
+    const float2 om = two_over2<true>(add2(v2(a.tau), sqrt2<true>(arg)));
     const float2 uu = fma2(uz, uz, fma2(uy, uy, mul2(ux, ux)));
     const float2 e = fms2(mul2(v2(1.5f), rho), uu, drho);
     if (LBM_RELAX_FOLD) {
@@ -714,7 +781,7 @@ LBM_HD float2 collide2_forced(float2 (&g)[Q], const StepArgs &a) {
     const float2 szz = mul2(is, add2(add2(add2(add2(s5, s9), s11), s15), s17));
     const float2 sxy = mul2(is, sub2(s7, s13)), sxz = mul2(is, sub2(s9, s15)), syz = mul2(is, sub2(s11, s17));
     const float2 rho = add2(v2(1.0f), drho);
-    const float2 irho = make_float2(1.0f / rho.x, 1.0f / rho.y);
+    const float2 irho = rcp2<false>(rho);
     // F = f + 2 Omega x j
     const float2 Fx = fma2(v2(2.0f), sub2(mul2(v2(a.oy), jz), mul2(v2(a.oz), jy)), v2(a.fx));
     const float2 Fy = fma2(v2(2.0f), sub2(mul2(v2(a.oz), jx), mul2(v2(a.ox), jz)), v2(a.fy));
@@ -730,8 +797,8 @@ LBM_HD float2 collide2_forced(float2 (&g)[Q], const StepArgs &a) {
     const float2 pd = fma2(pzz, pzz, fma2(pyy, pyy, mul2(pxx, pxx)));
     const float2 po = fma2(pyz, pyz, fma2(pxz, pxz, mul2(pxy, pxy)));
     const float2 pp2 = fma2(v2(4.0f), po, mul2(v2(2.0f), pd));   // 2 Pi:Pi
-    const float2 arg = fma2(mul2(v2(a.c2x18), irho), make_float2(sqrtf(pp2.x), sqrtf(pp2.y)), v2(a.tau * a.tau));
-    const float2 om = make_float2(2.0f / (a.tau + sqrtf(arg.x)), 2.0f / (a.tau + sqrtf(arg.y)));
+    const float2 arg = fma2(mul2(v2(a.c2x18), irho), sqrt2<false>(pp2), v2(a.tau * a.tau));
+    const float2 om = two_over2<false>(add2(v2(a.tau), sqrt2<false>(arg)));
     const float2 uu = fma2(uz, uz, fma2(uy, uy, mul2(ux, ux)));
     const float2 e = fms2(mul2(v2(1.5f), rho), uu, drho);
     // source coefficients: pre = (1 - om/2) S, uf = u.F
@@ -1024,6 +1091,12 @@ LBM_HD void store_side(const Geo &G, void *const *side, int x, int y, int z, con
 }
 
 LBM_HD void cell_coords(const Geo &G, long long n, int &x, int &y, int &z) {
+    if (G.N <= 0x7fffffffll) {   // 32-bit division (several times cheaper than 64-bit on the GPU)
+        const unsigned un = (unsigned)n, sz = (unsigned)G.sz, sy = (unsigned)G.sy;
+        const unsigned zz = un / sz, r = un - zz * sz, yy = r / sy;
+        z = (int)zz; y = (int)yy; x = (int)(r - yy * sy);
+        return;
+    }
     z = (int)(n / G.sz);
     const long long r = n - (long long)z * G.sz;
     y = (int)(r / G.sy);

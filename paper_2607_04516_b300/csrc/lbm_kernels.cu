@@ -86,13 +86,19 @@ __global__ void k_export(StepArgs a, bool layoutA, float *__restrict__ out) {
 // Pass 1: kRedBlocks blocks stride over the lattice; each thread accumulates its cells (diag_cell:
 // FP32 partials of the small per-cell terms) and each block writes 4 FP64 partials into scratch.
 // Pass 2: one block folds the partials.  Fixed block count -> deterministic result.
+// (4 resident blocks per SM: at one block, as the unbounded register count allowed, the pass was
+// latency-bound at a sixth of the HBM bandwidth)
 template <int S>
-__global__ void __launch_bounds__(kBlock) k_reduce_partial(StepArgs a, bool layoutA,
+__global__ void __launch_bounds__(kBlock, 4) k_reduce_partial(StepArgs a, bool layoutA,
                                                            double *__restrict__ part) {
     DiagAcc acc;
-    const long long stride = (long long)gridDim.x * kBlock;
-    for (long long n = (long long)blockIdx.x * kBlock + threadIdx.x; n < a.g.N; n += stride)
-        diag_cell<S>(a, n, layoutA, acc);
+    const long long stride = (long long)gridDim.x * kBlock, first = (long long)blockIdx.x * kBlock + threadIdx.x;
+    // cells off the face layers first; the face-layer cells, whose read-back of an odd step takes the
+    // general boundary resolution, in a second loop over the face enumeration, so that they fill
+    // whole warps instead of idling 31 lanes of the warps that hold one of them
+    for (long long n = first; n < a.g.N; n += stride)
+        if (!(a.flags[n] & F_FACE)) diag_cell<S>(a, n, layoutA, acc);
+    for (long long t = first; t < a.nface; t += stride) diag_face_cell<S>(a, t, layoutA, acc);
     diag_block_store<kBlock>(acc, part + 4 * blockIdx.x);
 }
 

@@ -65,18 +65,22 @@ cudaError_t scratch_for_current_device(double **out) {
     return cudaSuccess;
 }
 
-// Pass 1: block b reduces the cells [b * kCellsPerBlock, (b + 1) * kCellsPerBlock) into
-// part[4b .. 4b+3], with the per-cell rule and the block fold of lbm_diagnostics (diag_cell,
-// diag_block_store).
+// Pass 1: block b reduces the cells [b * kCellsPerBlock, (b + 1) * kCellsPerBlock) off the face
+// layers and its share of the face enumeration into part[4b .. 4b+3], with the per-cell rule and
+// the block fold of lbm_diagnostics (diag_cell, diag_block_store).
 template <int S>
-__global__ void __launch_bounds__(kBlockNa) k_na_partial(StepArgs a, bool layoutA, double *__restrict__ part) {
+__global__ void __launch_bounds__(kBlockNa, 4) k_na_partial(StepArgs a, bool layoutA, double *__restrict__ part) {
     DiagAcc acc;
     const long long base = (long long)blockIdx.x * kCellsPerBlock;
     for (int k = 0; k < kCellsPerThread; ++k) {
         const long long n = base + (long long)k * kBlockNa + threadIdx.x;
         if (n >= a.g.N) break;
-        diag_cell<S>(a, n, layoutA, acc);
+        if (!(a.flags[n] & F_FACE)) diag_cell<S>(a, n, layoutA, acc);
     }
+    // the face-layer cells, as in lbm_diagnostics: this block's share of the face enumeration
+    const long long fpb = (a.nface + gridDim.x - 1) / gridDim.x, t1 = (long long)(blockIdx.x + 1) * fpb;
+    for (long long t = (long long)blockIdx.x * fpb + threadIdx.x; t < t1 && t < a.nface; t += kBlockNa)
+        diag_face_cell<S>(a, t, layoutA, acc);
     diag_block_store<kBlockNa>(acc, part + 4 * blockIdx.x);
 }
 

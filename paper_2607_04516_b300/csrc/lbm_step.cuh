@@ -29,38 +29,60 @@ namespace lbm {
 #ifndef LBM_MIN_BLOCKS_FORCED16
 #define LBM_MIN_BLOCKS_FORCED16 4
 #endif
-template <int S, bool FORCE> constexpr int min_blocks(int unforced) {
-    return !FORCE ? unforced : (S == LBM_F32 ? LBM_MIN_BLOCKS_FORCED32 : LBM_MIN_BLOCKS_FORCED16);
+// The unforced FP32 two-cell kernels (lattices of at least kDual32MinCells cells): 3 blocks per SM,
+// whose 85 registers hold the pair collision with special-function reciprocals and square roots
+// without spilling (400 x 400 x 80 city on B300: neighbour 0.385 -> 0.371 ms, local 0.322 -> 0.313
+// ms against 4 blocks with the IEEE forms).
+#ifndef LBM_MIN_BLOCKS_DUAL32
+#define LBM_MIN_BLOCKS_DUAL32 3
+#endif
+template <int S, bool FORCE, bool D32 = false> constexpr int min_blocks(int unforced) {
+    return FORCE ? (S == LBM_F32 ? LBM_MIN_BLOCKS_FORCED32 : LBM_MIN_BLOCKS_FORCED16)
+                 : ((S == LBM_F32 && D32) ? LBM_MIN_BLOCKS_DUAL32 : unforced);
 }
 
 template <int S, bool FORCE, bool PACK, bool D32>
-__global__ void __launch_bounds__(kBlock, min_blocks<S, FORCE>(LBM_MIN_BLOCKS_LOCAL)) k_step_local(StepArgs a) {
+__global__ void __launch_bounds__(kBlock, min_blocks<S, FORCE, D32>(LBM_MIN_BLOCKS_LOCAL)) k_step_local(StepArgs a) {
     local_block<S, FORCE, PACK, D32>(a, blockIdx.x);
 }
 
-// Blocks [0, face_blocks) update the face-layer cells (general boundary resolution, ALU heavy);
-// the remaining blocks cover the lattice and update its interior cells.  Face blocks go first so
-// that their arithmetic overlaps the memory traffic of the interior blocks, and no warp mixes the
-// two paths.  The grid has one block per unit (units == gridDim.x); the 16-bit kernels are
+// face_blocks of the units update the face-layer cells (face tables or the general boundary
+// resolution, latency and ALU heavy), placed among the lattice blocks as unit_of says; the
+// remaining units cover the lattice and update its interior cells.  No warp mixes the two paths.  The grid has one block per unit (units == gridDim.x); the 16-bit kernels are
 // written as a loop over units all the same: on B300 that form of the code runs the 16-bit
 // neighbour step 3-5% faster (0.310 against 0.326 ms on the 400 x 400 x 80 city) and the FP32 one
 // 5% slower, so FP32 keeps the plain form.
 template <int S, bool FORCE, bool PACK, bool D32>
-__global__ void __launch_bounds__(kBlock, min_blocks<S, FORCE>(LBM_MIN_BLOCKS_NEIGHBOR)) k_step_neighbor(StepArgs a, unsigned face_blocks,
-                                                                                 unsigned units) {
+__global__ void __launch_bounds__(kBlock, min_blocks<S, FORCE, D32>(LBM_MIN_BLOCKS_NEIGHBOR)) k_step_neighbor(StepArgs a, unsigned face_blocks,
+                                                                                 unsigned units, int pshift, unsigned lb0) {
     if constexpr (S == LBM_F32) {
-        neighbor_block<S, FORCE, PACK, D32>(a, blockIdx.x, face_blocks);
+        neighbor_block<S, FORCE, PACK, D32>(a, blockIdx.x, face_blocks, pshift, lb0);
     } else {
-        for (unsigned b = blockIdx.x; b < units; b += gridDim.x) neighbor_block<S, FORCE, PACK, D32>(a, b, face_blocks);
+        for (unsigned b = blockIdx.x; b < units; b += gridDim.x) neighbor_block<S, FORCE, PACK, D32>(a, b, face_blocks, pshift, lb0);
     }
+}
+
+// The lattice blocks of the neighbour step that reach into the ground or top layer (zlat, two
+// cells per thread): [0, g1) and [t0, ...) of the lattice blocks, one launch block each.
+template <int S, bool FORCE, bool D32>
+__global__ void __launch_bounds__(kBlock, min_blocks<S, FORCE, D32>(LBM_MIN_BLOCKS_NEIGHBOR)) k_step_layers(StepArgs a, unsigned g1,
+                                                                               unsigned t0) {
+    const unsigned lb = blockIdx.x < g1 ? blockIdx.x : t0 + (blockIdx.x - g1);
+    constexpr long long span = (long long)cells_per_thread<S, D32>() * kBlock;
+    prefetch_ahead<S, D32, true, kBlock>(a, lb, lattice_blocks<S, D32, kBlock>(a.g.N));
+    neighbor_layer_unit<S, FORCE, D32, kBlock>(a, lb, block_layer_kind(a, lb, span), threadIdx.x);
 }
 
 template <int S, bool FORCE, bool PACK, bool D32>
 void step_p(bool neighbor, const StepArgs &a, cudaStream_t s) {
     const unsigned lb = lattice_blocks<S, D32>(a.g.N);
     if (neighbor) {
-        const unsigned fb = blocks_for(a.nface);
-        k_step_neighbor<S, FORCE, PACK, D32><<<fb + lb, kBlock, 0, s>>>(a, fb, fb + lb);
+        const unsigned fb = blocks_for(step_face_cells(a));
+        const LayerSplit ls = layer_split(a, (long long)cells_per_thread<S, D32>() * kBlock, lb);
+        const unsigned nl = lb - ls.g1 - (lb - ls.t0);   // lattice blocks of the main kernel
+        if (ls.g1 + (lb - ls.t0) > 0) k_step_layers<S, FORCE, D32><<<ls.g1 + (lb - ls.t0), kBlock, 0, s>>>(a, ls.g1, ls.t0);
+        if (fb + nl > 0)
+            k_step_neighbor<S, FORCE, PACK, D32><<<fb + nl, kBlock, 0, s>>>(a, fb, fb + nl, face_period_shift(fb, fb + nl), ls.g1);
     } else {
         k_step_local<S, FORCE, PACK, D32><<<lb, kBlock, 0, s>>>(a);
     }
