@@ -233,7 +233,14 @@ lbm_status lbm_batch_create(lbm_domain *const *domains, int n, void *workspace, 
             return LBM_EINVAL;   // mixed storage, forced, turbulent-inflow or repeated members
         }
         b->dom.push_back(d);
-        b->args.push_back(a);
+        // batched launches take the ground and top layers through the face blocks, as the
+        // single-domain step does without zlat: the layer blocks' own kernel (k_step_layers) has no
+        // batched form, and inlined into the batched kernels its variants cost their registers
+        // (every batched shape ran at half speed)
+        StepArgs ab = a;
+        ab.zlat = 0;
+        ab.nface_step = ab.nface;
+        b->args.push_back(ab);
     }
     if (batch_parity(b) < 0) {
         free_batch(b);

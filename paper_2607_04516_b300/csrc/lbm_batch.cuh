@@ -52,15 +52,18 @@ template <int S, int CPT> __device__ __forceinline__ bool batch_d32(const StepAr
 }
 
 // Block bid of a member's own launch of this step kind (the same block bodies as lbm_step).
-template <int S, bool NEIGHBOR, int B, int CPT>
+// FASTC: the FP32 pair collision takes the special-function reciprocals and square roots; the
+// batched kernels keep the IEEE forms (with the special-function forms they spilled 300-800 bytes a
+// thread at 3 and 4 blocks per SM).
+template <int S, bool NEIGHBOR, int B, int CPT, bool FASTC>
 __device__ __forceinline__ void batch_block(const StepArgs &a, unsigned bid) {
     const bool d32 = batch_d32<S, CPT>(a);
     if constexpr (NEIGHBOR) {
-        if (d32) neighbor_block<S, false, false, true, B, true>(a, bid, face_blocks_of<B>(step_face_cells(a)));
-        else neighbor_block<S, false, false, false, B, true>(a, bid, face_blocks_of<B>(step_face_cells(a)));
+        if (d32) neighbor_block<S, false, false, true, B, false, FASTC>(a, bid, face_blocks_of<B>(step_face_cells(a)));
+        else neighbor_block<S, false, false, false, B, false, FASTC>(a, bid, face_blocks_of<B>(step_face_cells(a)));
     } else if constexpr (S == LBM_F32) {
-        if (d32) local_block<S, false, false, true, B>(a, bid);
-        else local_block<S, false, false, false, B>(a, bid);
+        if (d32) local_block<S, false, false, true, B, FASTC>(a, bid);
+        else local_block<S, false, false, false, B, FASTC>(a, bid);
     } else {
         if (a.pack16) local_block<S, false, true, false, B>(a, bid);
         else local_block<S, false, false, false, B>(a, bid);
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_batch_step(BatchTables t) {
         for (int k = threadIdx.x; k < (int)(sizeof(StepArgs) / sizeof(int)); k += kBlock) dst[k] = src[k];
     }
     __syncthreads();
-    batch_block<S, NEIGHBOR, kBlock, 0>(sa, s_bid);
+    batch_block<S, NEIGHBOR, kBlock, 0, false>(sa, s_bid);
 }
 
 // Up to kParamMembers members: the step arguments and block tables travel in the kernel's parameter
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(B, MINB) k_batch_step_p(const __grid_constant_
             if (p.start[mid] <= vb) lo = mid;
             else hi = mid - 1;
         }
-        batch_block<S, NEIGHBOR, B, CPT>(p.args[p.member[lo]], vb - p.start[lo]);
+        batch_block<S, NEIGHBOR, B, CPT, false>(p.args[p.member[lo]], vb - p.start[lo]);
     }
 }
 

@@ -770,13 +770,14 @@ LBM_HD void cell2_neighbor_interior_dual(const StepArgs &a, int n0, int n1, bool
 // go through one collide2 (FP32x2 instructions).  Stores per cell, as in the one-cell kernels.
 
 // Collision of the pair: unforced, or with the body force and the zone nudging (FORCE).
-template <bool FORCE>
+// FAST: special-function reciprocals and square roots in the unforced collision (see rcp2)
+template <bool FORCE, bool FAST = true>
 LBM_HD void collide2_f32(const StepArgs &a, int n0, int n1, float2 (&g)[Q]) {
     if constexpr (FORCE) {
         const float2 drho = collide2_forced<0>(g, a);
         nudge2(a, n0, n1, drho, g);
     } else {
-        collide2<0>(g, a);
+        collide2<0, FAST>(g, a);
     }
 }
 
@@ -811,7 +812,7 @@ LBM_HD void cell2_local_store_f32(const StepArgs &a, int n0, int n1, uint8_t f0,
     }
 }
 
-template <bool FORCE = false>
+template <bool FORCE = false, bool FAST = true>
 LBM_HD void cell2_local_dual_f32(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
     float *const *P = (float *const *)a.plane;
     float2 g[Q];   // loaded before the flags are known (n1 may be past N: guard region)
@@ -819,7 +820,7 @@ LBM_HD void cell2_local_dual_f32(const StepArgs &a, int n0, int n1, bool v0, boo
     for (int i = 0; i < Q; ++i) g[i] = make_float2(ld_early_f32(P[i] + n0), ld_early_f32(P[i] + n1));
     const uint8_t f0 = v0 ? a.flags[n0] : F_SOLID, f1 = v1 ? a.flags[n1] : F_SOLID;
     if ((f0 & f1) & F_SOLID) return;
-    collide2_f32<FORCE>(a, n0, n1, g);
+    collide2_f32<FORCE, FAST>(a, n0, n1, g);
     if ((f0 | f1) & F_EQ) eq_lanes<0>(a, n0, n1, f0, f1, g);
     cell2_local_store_f32(a, n0, n1, f0, f1, g);
 }
@@ -848,7 +849,7 @@ LBM_HD void cell2_neighbor_store_f32(const StepArgs &a, int n0, int n1, bool l0,
     }
 }
 
-template <bool FORCE = false>
+template <bool FORCE = false, bool FAST = true>
 LBM_HD void cell2_neighbor_interior_dual_f32(const StepArgs &a, int n0, int n1, bool v0, bool v1) {
     float *const *P = (float *const *)a.plane;
     float2 g[Q];   // loaded before the flags are known (guard region after the planes)
@@ -860,7 +861,7 @@ LBM_HD void cell2_neighbor_interior_dual_f32(const StepArgs &a, int n0, int n1, 
     const uint8_t f0 = v0 ? a.flags[n0] : F_SOLID, f1 = v1 ? a.flags[n1] : F_SOLID;
     const bool l0 = !(f0 & (F_SOLID | F_FACE)), l1 = !(f1 & (F_SOLID | F_FACE));
     if (!l0 && !l1) return;
-    collide2_f32<FORCE>(a, n0, n1, g);
+    collide2_f32<FORCE, FAST>(a, n0, n1, g);
     cell2_neighbor_store_f32(a, n0, n1, l0, l1, f0, f1, g);
 }
 
@@ -1026,7 +1027,7 @@ LBM_HD void cell2_neighbor_layer_dual(const StepArgs &a, int n0, bool v1) {
 }
 
 // FP32 storage, cells n0 and n0 + D of a ground or top block.
-template <bool FORCE, int ZK, int D>
+template <bool FORCE, int ZK, int D, bool FAST = true>
 LBM_HD void cell2_neighbor_layer_dual_f32(const StepArgs &a, int n0, bool v1) {
     const int n1 = n0 + D;
     float2 g[Q];   // loaded before the flags are known (guard region after the planes)
@@ -1043,7 +1044,7 @@ LBM_HD void cell2_neighbor_layer_dual_f32(const StepArgs &a, int n0, bool v1) {
         neighbor_zl_cells<LBM_F32, FORCE>(a, n0, n1, v1);
         return;
     }
-    collide2_f32<FORCE>(a, n0, n1, g);
+    collide2_f32<FORCE, FAST>(a, n0, n1, g);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         if (!(c ? l1 : l0)) continue;
@@ -1327,14 +1328,15 @@ __device__ __forceinline__ void prefetch_ahead(const StepArgs &a, unsigned lb, u
     prefetch_l2(base, end, p + c0 * sb, p + (c0 + span) * sb);
 }
 
-// B: threads per block (the kernels use kBlock; batched launches may choose another size)
-template <int S, bool FORCE, bool PACK, bool D32 = false, int B = kBlock>
+// B: threads per block (the kernels use kBlock; batched launches may choose another size).
+// FASTC: the FP32 pair collision takes the special-function forms (kernels at <= 3 blocks per SM).
+template <int S, bool FORCE, bool PACK, bool D32 = false, int B = kBlock, bool FASTC = true>
 __device__ __forceinline__ void local_block(const StepArgs &a, unsigned bid) {
     prefetch_ahead<S, D32, false, B>(a, bid, lattice_blocks<S, D32, B>(a.g.N));
     if constexpr (S == LBM_F32 && cells_per_thread<S, D32>() == 2) {
         const int n0 = (int)(bid * 2 * B + threadIdx.x), n1 = n0 + B;
         if (n0 >= a.g.N) return;
-        cell2_local_dual_f32<FORCE>(a, n0, n1, true, n1 < a.g.N);
+        cell2_local_dual_f32<FORCE, FASTC>(a, n0, n1, true, n1 < a.g.N);
     } else if constexpr (cells_per_thread<S, D32>() == 1) {
         const int n = (int)(bid * B + threadIdx.x);
         if (n >= a.g.N) return;
@@ -1486,7 +1488,7 @@ __device__ __forceinline__ unsigned unit_of(unsigned u, unsigned fb, int pshift,
 // unit: this block's place in the launch; the lattice blocks of the launch start at lattice block
 // lb0.  LAYERS: the launch also covers the ground and top blocks (zlat), handled through
 // neighbor_layer_unit, inline (the single-domain step gives them to k_step_layers instead).
-template <int S, bool FORCE, bool PACK, bool D32 = false, int B = kBlock, bool LAYERS = false>
+template <int S, bool FORCE, bool PACK, bool D32 = false, int B = kBlock, bool LAYERS = false, bool FASTC = true>
 __device__ __forceinline__ void neighbor_block(const StepArgs &a, unsigned unit, unsigned face_blocks, int pshift = -1,
                                                unsigned lb0 = 0) {
     bool face;
@@ -1507,7 +1509,7 @@ __device__ __forceinline__ void neighbor_block(const StepArgs &a, unsigned unit,
         if constexpr (S == LBM_F32 && cells_per_thread<S, D32>() == 2) {
             const int n0 = (int)((bid - face_blocks) * 2 * B + threadIdx.x), n1 = n0 + B;
             if (n0 >= a.g.N) return;
-            cell2_neighbor_interior_dual_f32<FORCE>(a, n0, n1, true, n1 < a.g.N);
+            cell2_neighbor_interior_dual_f32<FORCE, FASTC>(a, n0, n1, true, n1 < a.g.N);
         } else if constexpr (cells_per_thread<S, D32>() == 1) {
             const int n = (int)((bid - face_blocks) * B + threadIdx.x);
             if (n >= a.g.N) return;

@@ -661,7 +661,7 @@ LBM_HD void collide2_relax(const Relax2 &r, Get get, Put put) {
 
 // Two cells held as float pairs (FP32 storage): the moments as one balanced sum tree (more
 // independent instructions in flight than the pair-by-pair accumulation, measured faster there).
-template <int LOG2S>
+template <int LOG2S, bool FAST = true>
 LBM_HD void collide2(float2 (&g)[Q], const StepArgs &a) {
     constexpr float S = (float)(1 << LOG2S), iS = 1.0f / S;
     const float2 s1 = add2(g[1], g[2]), d1 = sub2(g[1], g[2]);
@@ -685,7 +685,7 @@ LBM_HD void collide2(float2 (&g)[Q], const StepArgs &a) {
     const float2 sxy = sub2(s7, s13), sxz = sub2(s9, s15), syz = sub2(s11, s17);
     const float2 drho = LOG2S ? mul2(v2(iS), m0) : m0;
     const float2 rho = add2(v2(1.0f), drho);
-    const float2 irho = rcp2<true>(rho);
+    const float2 irho = rcp2<FAST>(rho);
     const float2 irs = LOG2S ? mul2(v2(iS), irho) : irho;
     const float2 ux = mul2(jx, irs), uy = mul2(jy, irs), uz = mul2(jz, irs);
     const float2 d3r = mul2(m0, v2(1.0f / 3.0f));
@@ -695,8 +695,8 @@ LBM_HD void collide2(float2 (&g)[Q], const StepArgs &a) {
     const float2 pd = fma2(pzz, pzz, fma2(pyy, pyy, mul2(pxx, pxx)));
     const float2 po = fma2(pyz, pyz, fma2(pxz, pxz, mul2(pxy, pxy)));
     const float2 pp2 = fma2(v2(4.0f), po, mul2(v2(2.0f), pd));   // 2 Pi:Pi (times S^2)
-    const float2 arg = fma2(mul2(v2(a.c2x18 * iS), irho), sqrt2<true>(pp2), v2(a.tau * a.tau));
-    const float2 om = two_over2<true>(add2(v2(a.tau), sqrt2<true>(arg)));
+    const float2 arg = fma2(mul2(v2(a.c2x18 * iS), irho), sqrt2<FAST>(pp2), v2(a.tau * a.tau));
+    const float2 om = two_over2<FAST>(add2(v2(a.tau), sqrt2<FAST>(arg)));
     const float2 uu = fma2(uz, uz, fma2(uy, uy, mul2(ux, ux)));
     const float2 e = fms2(mul2(v2(1.5f), rho), uu, drho);
     if (LBM_RELAX_FOLD) {
