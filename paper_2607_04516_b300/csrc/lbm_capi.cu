@@ -17,6 +17,11 @@
 
 using namespace lbm;
 
+// the neighbour step's layer kernel on a second stream of the domain (1), or in order (0)
+#ifndef LBM_STEP_AUX
+#define LBM_STEP_AUX 1
+#endif
+
 namespace {
 
 constexpr size_t kAlign = 256;
@@ -129,11 +134,17 @@ struct lbm_domain {
     float *ub_pinned = nullptr;
     cudaEvent_t ub_done[kStage];
     int ub_slot;
+    StepAux aux;                 // second stream for the neighbour step's layer kernel (null: none)
     char err[512];
     ~lbm_domain() {
         if (ub_pinned) {
             for (int k = 0; k < kStage; ++k) cudaEventDestroy(ub_done[k]);
             cudaFreeHost(ub_pinned);
+        }
+        if (aux.stream) {
+            cudaEventDestroy(aux.fork);
+            cudaEventDestroy(aux.join);
+            cudaStreamDestroy(aux.stream);
         }
     }
 };
@@ -422,6 +433,19 @@ lbm_status lbm_create_domain(const uint8_t *solid, int nx, int ny, int nz, const
         }
         cudaGetLastError();   // a failed pinned allocation only means pageable uploads
     }
+    {   // the layer kernel's stream (see StepAux); without it the step runs its kernels in order
+        StepAux x;
+        if (LBM_STEP_AUX && cudaStreamCreateWithFlags(&x.stream, cudaStreamNonBlocking) == cudaSuccess) {
+            if (cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) == cudaSuccess) {
+                d->aux = x;
+            } else {
+                if (x.fork) cudaEventDestroy(x.fork);
+                cudaStreamDestroy(x.stream);
+            }
+        }
+        cudaGetLastError();
+    }
     for (int k = 0; k < 6; ++k) {
         // face plane k: (y, z), (x, z) or (x, y), first index fastest
         const int a = k / 2, hi = k & 1;
@@ -567,7 +591,7 @@ lbm_status lbm_step(lbm_domain *d, int n) {
             s.alpha = interp ? (float)(t - ta) / (float)sp : 0.0f;
         }
         const StepArgs a = args_of(d);
-        launch_step(d->p.store, (d->t & 1) == 0, force, a, d->stream);
+        launch_step(d->p.store, (d->t & 1) == 0, force, a, d->stream, &d->aux);
         d->t += 1;
         if (d->p.watchdog_every > 0 && d->t % d->p.watchdog_every == 0) {
             double diag[4];

@@ -15,9 +15,17 @@ inline unsigned blocks_for(long long n) { return (unsigned)((n + 255) / 256); }
 cudaError_t launch_flags(const uint8_t *mask, uint8_t *flags, uint32_t *info, const Geo &G, cudaStream_t s);
 cudaError_t launch_init(int store, const StepArgs &a, const float *rho, const float *u, cudaStream_t s);
 cudaError_t launch_import(int store, const StepArgs &a, const float *g, cudaStream_t s);
-void launch_step(int store, bool neighbor, bool force, const StepArgs &a, cudaStream_t s);
+// A second stream and two events of a domain: the neighbour step's layer kernel (k_step_layers) runs
+// on it concurrently with the main kernel, forked from and joined back into the step's stream (the
+// two kernels touch disjoint memory: in the in-place scheme every location a neighbour step reads is
+// written by the same thread).  stream == null: both kernels in order on the step's stream.
+struct StepAux {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+void launch_step(int store, bool neighbor, bool force, const StepArgs &a, cudaStream_t s, const StepAux *aux = nullptr);
 // The step launch of one storage type and forcing (defined in lbm_step_kern.cu, one object each).
-template <int S, bool FORCE> void launch_step_sf(bool neighbor, const StepArgs &a, cudaStream_t s);
+template <int S, bool FORCE> void launch_step_sf(bool neighbor, const StepArgs &a, cudaStream_t s, const StepAux *aux);
 cudaError_t launch_macros(int store, const StepArgs &a, bool layoutA, float *rho, float *u,
                           cudaStream_t s);
 cudaError_t launch_sample(int store, const StepArgs &a, bool layoutA, const int *ij, int ncol,

@@ -161,11 +161,11 @@ cudaError_t launch_import(int store, const StepArgs &a, const float *g, cudaStre
 }
 
 // one object per (storage, forced) pair holds the step kernels (lbm_step_kern.cu)
-void launch_step(int store, bool neighbor, bool force, const StepArgs &a, cudaStream_t s) {
+void launch_step(int store, bool neighbor, bool force, const StepArgs &a, cudaStream_t s, const StepAux *aux) {
     switch (store) {
-        case LBM_F32: force ? launch_step_sf<LBM_F32, true>(neighbor, a, s) : launch_step_sf<LBM_F32, false>(neighbor, a, s); break;
-        case LBM_F16S: force ? launch_step_sf<LBM_F16S, true>(neighbor, a, s) : launch_step_sf<LBM_F16S, false>(neighbor, a, s); break;
-        default: force ? launch_step_sf<LBM_BF16S, true>(neighbor, a, s) : launch_step_sf<LBM_BF16S, false>(neighbor, a, s); break;
+        case LBM_F32: force ? launch_step_sf<LBM_F32, true>(neighbor, a, s, aux) : launch_step_sf<LBM_F32, false>(neighbor, a, s, aux); break;
+        case LBM_F16S: force ? launch_step_sf<LBM_F16S, true>(neighbor, a, s, aux) : launch_step_sf<LBM_F16S, false>(neighbor, a, s, aux); break;
+        default: force ? launch_step_sf<LBM_BF16S, true>(neighbor, a, s, aux) : launch_step_sf<LBM_BF16S, false>(neighbor, a, s, aux); break;
     }
 }
 

@@ -74,15 +74,21 @@ __global__ void __launch_bounds__(kBlock, min_blocks<S, FORCE, D32>(LBM_MIN_BLOC
 }
 
 template <int S, bool FORCE, bool PACK, bool D32>
-void step_p(bool neighbor, const StepArgs &a, cudaStream_t s) {
+void step_p(bool neighbor, const StepArgs &a, cudaStream_t s, const StepAux *aux) {
     const unsigned lb = lattice_blocks<S, D32>(a.g.N);
     if (neighbor) {
         const unsigned fb = blocks_for(step_face_cells(a));
         const LayerSplit ls = layer_split(a, (long long)cells_per_thread<S, D32>() * kBlock, lb);
-        const unsigned nl = lb - ls.g1 - (lb - ls.t0);   // lattice blocks of the main kernel
-        if (ls.g1 + (lb - ls.t0) > 0) k_step_layers<S, FORCE, D32><<<ls.g1 + (lb - ls.t0), kBlock, 0, s>>>(a, ls.g1, ls.t0);
+        const unsigned nl = ls.t0 - ls.g1, nlay = ls.g1 + (lb - ls.t0);   // main / layer kernel lattice blocks
+        // the layer kernel forked onto the domain's second stream when there is one (its launch
+        // overlaps the main kernel instead of adding its ramp and tail), else in order
+        const bool fork = nlay > 0 && fb + nl > 0 && aux && aux->stream &&
+                          cudaEventRecord(aux->fork, s) == cudaSuccess && cudaStreamWaitEvent(aux->stream, aux->fork, 0) == cudaSuccess;
+        if (nlay > 0) k_step_layers<S, FORCE, D32><<<nlay, kBlock, 0, fork ? aux->stream : s>>>(a, ls.g1, ls.t0);
+        if (fork) cudaEventRecord(aux->join, aux->stream);
         if (fb + nl > 0)
             k_step_neighbor<S, FORCE, PACK, D32><<<fb + nl, kBlock, 0, s>>>(a, fb, fb + nl, face_period_shift(fb, fb + nl), ls.g1);
+        if (fork) cudaStreamWaitEvent(s, aux->join, 0);
     } else {
         k_step_local<S, FORCE, PACK, D32><<<lb, kBlock, 0, s>>>(a);
     }
@@ -92,13 +98,13 @@ void step_p(bool neighbor, const StepArgs &a, cudaStream_t s) {
 // neighbour step the (n, n + 256) pairs (faster for its shifted accesses, measured on B300).
 // FP32 storage: two cells per thread on lattices of at least kDual32MinCells cells.
 template <int S, bool FORCE>
-void step_t(bool neighbor, const StepArgs &a, cudaStream_t s) {
+void step_t(bool neighbor, const StepArgs &a, cudaStream_t s, const StepAux *aux) {
     if constexpr (S == LBM_F32) {
-        if (a.g.N >= kDual32MinCells) step_p<S, FORCE, false, true>(neighbor, a, s);
-        else step_p<S, FORCE, false, false>(neighbor, a, s);
+        if (a.g.N >= kDual32MinCells) step_p<S, FORCE, false, true>(neighbor, a, s, aux);
+        else step_p<S, FORCE, false, false>(neighbor, a, s, aux);
     } else {
-        if (a.pack16 && !neighbor) step_p<S, FORCE, true, false>(neighbor, a, s);
-        else step_p<S, FORCE, false, false>(neighbor, a, s);
+        if (a.pack16 && !neighbor) step_p<S, FORCE, true, false>(neighbor, a, s, aux);
+        else step_p<S, FORCE, false, false>(neighbor, a, s, aux);
     }
 }
 

@@ -9,8 +9,8 @@
 namespace lbm {
 
 template <>
-void launch_step_sf<LBM_INST_S, (LBM_INST_FORCE != 0)>(bool neighbor, const StepArgs &a, cudaStream_t s) {
-    step_t<LBM_INST_S, (LBM_INST_FORCE != 0)>(neighbor, a, s);
+void launch_step_sf<LBM_INST_S, (LBM_INST_FORCE != 0)>(bool neighbor, const StepArgs &a, cudaStream_t s, const StepAux *aux) {
+    step_t<LBM_INST_S, (LBM_INST_FORCE != 0)>(neighbor, a, s, aux);
 }
 
 }  // namespace lbm
