@@ -385,3 +385,32 @@ def test_city_400x400x80_long_run_checks():
         err = float(torch.linalg.vector_norm((u - u32)[fl].double()) / torch.linalg.vector_norm(u32[fl].double()))
         print(f"city {store} vs f32 after 50 steps: rel L2 u = {err:.2e}")
         assert err <= tol
+
+
+@pytest.mark.parametrize("store", ["f16s", "f32"])
+def test_steps_captured_in_a_cuda_graph_replay_like_direct_steps(store):
+    """lbm_step enqueued during a CUDA-graph capture of the domain's stream (the neighbour step's
+    ground/top layer kernel forks onto the domain's second stream and joins back: the capture must
+    take it in) replays to the same populations, bit for bit, as the same steps launched directly.
+    A 16-bit lattice of any size, and an FP32 lattice of at least 2^21 cells, take the layer kernel."""
+    import torch
+    case = synth.city_case(nx=160 if store == "f32" else 64, ny=128 if store == "f32" else 48,
+                           nz=104 if store == "f32" else 16, seed=5)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        dom = gpu_domain(case, store, stream=s)
+        ref = gpu_domain(case, store, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        dom.step(2)                       # a neighbour and a local step
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            g.replay()
+        ref.step(6)
+    torch.cuda.synchronize()
+    assert dom.steps_done == 2            # the host counter saw the captured steps only
+    a = dom.export_populations().cpu().numpy()
+    b = ref.export_populations().cpu().numpy()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a, b)
