@@ -866,12 +866,14 @@ LBM_HD void cell2_neighbor_interior_dual_f32(const StepArgs &a, int n0, int n1, 
 }
 
 // ---------------------------------------------------------------- ground and top layers in the lattice blocks
-// With zlat, a lattice block of the neighbour step whose cells reach into the ground or top layer
-// updates both cells of each thread here: interior cells as cell_neighbor_interior does, F_ZL
-// cells with the rules of cell_neighbor_zlayer (the links crossing a no-slip face bounce back, those
-// crossing a free-slip face reflect specularly within the layer; a solid mirrored source bounces
-// back), both lanes through one paired collision.  The layer of a cell (1: ground, 2: top, 0: other)
-// follows from its index, so every load is issued before the flags are known.
+// With zlat the neighbour step updates the ground and top layer cells with interior x and y (F_ZL)
+// in lattice blocks.  The per-cell form, cell2_neighbor_zl, serves the blocks that straddle a layer
+// boundary (and free-slip layer cells next to a solid): both cells of each thread, interior cells
+// as cell_neighbor_interior does, F_ZL cells with the rules of cell_neighbor_zlayer (the links
+// crossing a no-slip face bounce back, those crossing a free-slip face reflect specularly within the
+// layer; a solid mirrored source bounces back), both lanes through one paired collision.  The layer
+// of a cell (1: ground, 2: top, 0: other) follows from its index, so every load is issued before the
+// flags are known.  Blocks wholly in one layer take the static rules further below.
 
 // Storage element that the neighbour step gathers direction i of cell n from (layer zl).
 LBM_HD long long zl_gather_elem(const StepArgs &a, long long n, int zl, int i) {
@@ -1422,7 +1424,7 @@ LBM_HD void neighbor_layer_unit(const StepArgs &a, unsigned lb, int zk, unsigned
 }
 
 // The lattice blocks of the neighbour step take the ground and top layers (zlat): 1, or 0 to leave
-// them to the face blocks.
+// them to the face blocks (measured: the layer kernel is faster, see k_step_layers).
 #ifndef LBM_ZLAT
 #define LBM_ZLAT 1
 #endif
