@@ -319,10 +319,13 @@ LBM_HD float sqrt_nonneg_fast(float x) { return x > 0.0f ? sqrt_pos_fast(x) : 0.
 
 // Reciprocals and square roots of the pair collisions.  FAST = true: single special-function-unit
 // instructions (rcp.approx / sqrt.approx, relative error ~2^-22, far below the FP32 rounding a step
-// accumulates anyway) with no slow-path branch -- the FP32-storage pair collision (collide2), whose
-// kernels run at 3 blocks per SM; FAST = false: the IEEE forms -- the 16-bit pair collision, where at
-// 4 blocks per SM the branch-free forms made the compiler spill (measured slower on B300).  Host
-// builds take the exact forms.  LBM_FAST2 = 0 / 1 forces one form everywhere (for measurements).
+// accumulates anyway) with no slow-path branch; FAST = false: the IEEE forms.  The FP32-storage pair
+// collision (collide2, kernels at 3 blocks per SM) takes the fast forms throughout; the 16-bit pair
+// collision (collide2_moments, 4 blocks per SM) takes them for 1/rho and the two square roots and
+// keeps the IEEE division of 2 / (tau + ...): with all three branch-free the compiler spilled 320
+// bytes a thread (16-bit steps 37.6 GLUPS), with these two 53.9 against 52.2 for all-IEEE (400 x 400
+// x 80 city, B300).  Host builds take the exact forms.  LBM_FAST2 = 0 / 1 forces one form everywhere
+// (for measurements).
 #ifndef LBM_FAST2
 #define LBM_FAST2 -1
 #endif
@@ -577,7 +580,7 @@ LBM_HD Relax2 collide2_moments(Get get, const StepArgs &a) {
     const float2 drho = LOG2S ? mul2(v2(iS), m0) : m0;
     const float2 rho = add2(v2(1.0f), drho);
     Relax2 r;
-    const float2 irho = rcp2<false>(rho);
+    const float2 irho = rcp2<true>(rho);
     const float2 irs = LOG2S ? mul2(v2(iS), irho) : irho;
     r.ux = mul2(jx, irs); r.uy = mul2(jy, irs); r.uz = mul2(jz, irs);
     const float2 d3r = mul2(m0, v2(1.0f / 3.0f));
@@ -587,8 +590,8 @@ LBM_HD Relax2 collide2_moments(Get get, const StepArgs &a) {
     const float2 pd = fma2(pzz, pzz, fma2(pyy, pyy, mul2(pxx, pxx)));
     const float2 po = fma2(pyz, pyz, fma2(pxz, pxz, mul2(pxy, pxy)));
     const float2 pp2 = fma2(v2(4.0f), po, mul2(v2(2.0f), pd));   // 2 Pi:Pi (times S^2)
-    const float2 arg = fma2(mul2(v2(a.c2x18 * iS), irho), sqrt2<false>(pp2), v2(a.tau * a.tau));
-    const float2 om = two_over2<false>(add2(v2(a.tau), sqrt2<false>(arg)));
+    const float2 arg = fma2(mul2(v2(a.c2x18 * iS), irho), sqrt2<true>(pp2), v2(a.tau * a.tau));
+    const float2 om = two_over2<false>(add2(v2(a.tau), sqrt2<true>(arg)));
     const float2 uu = fma2(r.uz, r.uz, fma2(r.uy, r.uy, mul2(r.ux, r.ux)));
     const float2 e = fms2(mul2(v2(1.5f), rho), uu, drho);
     if (LBM_RELAX_FOLD) {
