@@ -659,7 +659,7 @@ LBM_HD void collide2_packed_forced(const StepArgs &a, int n0, int n1, uint8_t f0
     float2 g[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) g[i] = Cd::template dec2<0>(pk[i]);
-    const float2 drho = collide2_forced<0>(g, a);
+    const float2 drho = collide2_forced<0, 3>(g, a);
     nudge2(a, n0, n1, drho, g);
     if ((f0 | f1) & F_EQ) eq_lanes<0>(a, n0, n1, f0, f1, g);
 #pragma unroll
@@ -770,11 +770,11 @@ LBM_HD void cell2_neighbor_interior_dual(const StepArgs &a, int n0, int n1, bool
 // go through one collide2 (FP32x2 instructions).  Stores per cell, as in the one-cell kernels.
 
 // Collision of the pair: unforced, or with the body force and the zone nudging (FORCE).
-// FAST: special-function reciprocals and square roots in the unforced collision (see rcp2)
+// FAST: special-function reciprocals and square roots in the collision (see rcp2, collide2_forced)
 template <bool FORCE, bool FAST = true>
 LBM_HD void collide2_f32(const StepArgs &a, int n0, int n1, float2 (&g)[Q]) {
     if constexpr (FORCE) {
-        const float2 drho = collide2_forced<0>(g, a);
+        const float2 drho = collide2_forced<0, FAST ? 7 : 0>(g, a);
         nudge2(a, n0, n1, drho, g);
     } else {
         collide2<0, FAST>(g, a);

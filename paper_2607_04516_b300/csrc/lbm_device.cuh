@@ -761,7 +761,11 @@ LBM_HD void collide2(float2 (&g)[Q], const StepArgs &a) {
 // populations.  On an opposite pair (c_j = -c_i) the source splits like the equilibrium into a
 // shared even part (1 - om/2) w (9 (c.u)(c.F) - 3 u.F) and an odd part +-(1 - om/2) 3 w c.F.  The
 // same arithmetic per lane as the one-cell form up to the order of rounding.  Returns drho.
-template <int LOG2S>
+// FM: the special-function forms (see rcp2) for 1/rho (bit 0), the square roots (bit 1) and the
+// division 2 / (tau + ...) (bit 2): all three for the FP32 two-cell kernels (3 blocks per SM), the
+// first two for the 16-bit ones (4 blocks per SM: with all three the compiler spills); measured on
+// B300, 400 x 400 x 80 city: FP32 zones 31.7 -> 33.1, FP16S with every physics term 33.6 -> 35.5 GLUPS.
+template <int LOG2S, int FM = 0>
 LBM_HD float2 collide2_forced(float2 (&g)[Q], const StepArgs &a) {
     constexpr float S = (float)(1 << LOG2S), iS = 1.0f / S;
     const float2 s1 = add2(g[1], g[2]), d1 = sub2(g[1], g[2]);
@@ -784,7 +788,7 @@ LBM_HD float2 collide2_forced(float2 (&g)[Q], const StepArgs &a) {
     const float2 szz = mul2(is, add2(add2(add2(add2(s5, s9), s11), s15), s17));
     const float2 sxy = mul2(is, sub2(s7, s13)), sxz = mul2(is, sub2(s9, s15)), syz = mul2(is, sub2(s11, s17));
     const float2 rho = add2(v2(1.0f), drho);
-    const float2 irho = rcp2<false>(rho);
+    const float2 irho = rcp2<(FM & 1) != 0>(rho);
     // F = f + 2 Omega x j
     const float2 Fx = fma2(v2(2.0f), sub2(mul2(v2(a.oy), jz), mul2(v2(a.oz), jy)), v2(a.fx));
     const float2 Fy = fma2(v2(2.0f), sub2(mul2(v2(a.oz), jx), mul2(v2(a.ox), jz)), v2(a.fy));
@@ -800,8 +804,8 @@ LBM_HD float2 collide2_forced(float2 (&g)[Q], const StepArgs &a) {
     const float2 pd = fma2(pzz, pzz, fma2(pyy, pyy, mul2(pxx, pxx)));
     const float2 po = fma2(pyz, pyz, fma2(pxz, pxz, mul2(pxy, pxy)));
     const float2 pp2 = fma2(v2(4.0f), po, mul2(v2(2.0f), pd));   // 2 Pi:Pi
-    const float2 arg = fma2(mul2(v2(a.c2x18), irho), sqrt2<false>(pp2), v2(a.tau * a.tau));
-    const float2 om = two_over2<false>(add2(v2(a.tau), sqrt2<false>(arg)));
+    const float2 arg = fma2(mul2(v2(a.c2x18), irho), sqrt2<(FM & 2) != 0>(pp2), v2(a.tau * a.tau));
+    const float2 om = two_over2<(FM & 4) != 0>(add2(v2(a.tau), sqrt2<(FM & 2) != 0>(arg)));
     const float2 uu = fma2(uz, uz, fma2(uy, uy, mul2(ux, ux)));
     const float2 e = fms2(mul2(v2(1.5f), rho), uu, drho);
     // source coefficients: pre = (1 - om/2) S, uf = u.F
