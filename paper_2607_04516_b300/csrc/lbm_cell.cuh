@@ -782,7 +782,9 @@ LBM_HD void collide2_f32(const StepArgs &a, int n0, int n1, float2 (&g)[Q]) {
 }
 
 // The local step's per-cell stores of a collided FP32 pair (solid lanes skipped, store-side
-// bounce-back links, outflow side copies).
+// bounce-back links, outflow side copies).  Every link goes to the cell's own reversed slot; a link
+// into a solid neighbour also goes to that neighbour's slot (the own slot of such a link is read by
+// nobody: the only cell that would gather it is the solid neighbour).
 LBM_HD void cell2_local_store_f32(const StepArgs &a, int n0, int n1, uint8_t f0, uint8_t f1, const float2 (&g)[Q]) {
     float *const *P = (float *const *)a.plane;
 #pragma unroll
@@ -790,16 +792,13 @@ LBM_HD void cell2_local_store_f32(const StepArgs &a, int n0, int n1, uint8_t f0,
         const uint8_t fl = c ? f1 : f0;
         if (fl & F_SOLID) continue;
         const int n = c ? n1 : n0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) P[opp(i)][n] = c ? g[i].y : g[i].x;
         if (fl & F_REDIR) {
             const unsigned nb = a.info[n] >> 8;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const bool bb = (nb >> i) & 1u;
-                (bb ? P[i] : P[opp(i)])[bb ? n + a.off[i] : n] = c ? g[i].y : g[i].x;
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) P[opp(i)][n] = c ? g[i].y : g[i].x;
+            for (int i = 0; i < Q; ++i)
+                if ((nb >> i) & 1u) P[i][n + a.off[i]] = c ? g[i].y : g[i].x;
         }
         if (fl & F_ZG) {
             float gc[Q];
@@ -826,7 +825,10 @@ LBM_HD void cell2_local_dual_f32(const StepArgs &a, int n0, int n1, bool v0, boo
 }
 
 // The neighbour step's per-cell scatter of a collided FP32 pair (l0 / l1: the lane takes this path;
-// a population heading into a solid goes to the cell's own reversed slot).
+// a population heading into a solid goes to the cell's own reversed slot).  Every link is scattered
+// downstream; a link into a solid neighbour also goes to the own reversed slot.  Its downstream
+// store lands in the solid's slot that this same cell gathered its bounce-back from earlier in the
+// step, which nothing else reads before the next local step rewrites it.
 LBM_HD void cell2_neighbor_store_f32(const StepArgs &a, int n0, int n1, bool l0, bool l1, uint8_t f0, uint8_t f1,
                                      const float2 (&g)[Q]) {
     float *const *P = (float *const *)a.plane;
@@ -835,16 +837,13 @@ LBM_HD void cell2_neighbor_store_f32(const StepArgs &a, int n0, int n1, bool l0,
         if (!(c ? l1 : l0)) continue;
         const int n = c ? n1 : n0;
         const uint8_t fl = c ? f1 : f0;
-        const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
-        if (nb) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const bool bb = (nb >> i) & 1u;
-                (bb ? P[opp(i)] : P[i])[bb ? n : n + a.off[i]] = c ? g[i].y : g[i].x;
-            }
-        } else {
+        for (int i = 0; i < Q; ++i) P[i][n + a.off[i]] = c ? g[i].y : g[i].x;
+        if (fl & F_REDIR) {
+            const unsigned nb = a.info[n] >> 8;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) P[i][n + a.off[i]] = c ? g[i].y : g[i].x;
+            for (int i = 0; i < Q; ++i)
+                if ((nb >> i) & 1u) P[opp(i)][n] = c ? g[i].y : g[i].x;
         }
     }
 }
