@@ -782,9 +782,12 @@ LBM_HD void collide2_f32(const StepArgs &a, int n0, int n1, float2 (&g)[Q]) {
 }
 
 // The local step's per-cell stores of a collided FP32 pair (solid lanes skipped, store-side
-// bounce-back links, outflow side copies).  Every link goes to the cell's own reversed slot; a link
-// into a solid neighbour also goes to that neighbour's slot (the own slot of such a link is read by
-// nobody: the only cell that would gather it is the solid neighbour).
+// bounce-back links, outflow side copies).  PLAIN: every link goes to the cell's own reversed slot
+// and a link into a solid neighbour also goes to that neighbour's slot (the own slot of such a link
+// is read by nobody: the only cell that would gather it is the solid neighbour); else a cell with
+// solid neighbours selects one target per link.  The single-domain kernels take the first form, the
+// batched ones (other register budgets, where it measured slower) the second.
+template <bool PLAIN = true>
 LBM_HD void cell2_local_store_f32(const StepArgs &a, int n0, int n1, uint8_t f0, uint8_t f1, const float2 (&g)[Q]) {
     float *const *P = (float *const *)a.plane;
 #pragma unroll
@@ -792,13 +795,25 @@ LBM_HD void cell2_local_store_f32(const StepArgs &a, int n0, int n1, uint8_t f0,
         const uint8_t fl = c ? f1 : f0;
         if (fl & F_SOLID) continue;
         const int n = c ? n1 : n0;
+        if (PLAIN) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) P[opp(i)][n] = c ? g[i].y : g[i].x;
-        if (fl & F_REDIR) {
+            for (int i = 0; i < Q; ++i) P[opp(i)][n] = c ? g[i].y : g[i].x;
+            if (fl & F_REDIR) {
+                const unsigned nb = a.info[n] >> 8;
+#pragma unroll
+                for (int i = 0; i < Q; ++i)
+                    if ((nb >> i) & 1u) P[i][n + a.off[i]] = c ? g[i].y : g[i].x;
+            }
+        } else if (fl & F_REDIR) {
             const unsigned nb = a.info[n] >> 8;
 #pragma unroll
-            for (int i = 0; i < Q; ++i)
-                if ((nb >> i) & 1u) P[i][n + a.off[i]] = c ? g[i].y : g[i].x;
+            for (int i = 0; i < Q; ++i) {
+                const bool bb = (nb >> i) & 1u;
+                (bb ? P[i] : P[opp(i)])[bb ? n + a.off[i] : n] = c ? g[i].y : g[i].x;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) P[opp(i)][n] = c ? g[i].y : g[i].x;
         }
         if (fl & F_ZG) {
             float gc[Q];
@@ -821,14 +836,16 @@ LBM_HD void cell2_local_dual_f32(const StepArgs &a, int n0, int n1, bool v0, boo
     if ((f0 & f1) & F_SOLID) return;
     collide2_f32<FORCE, FAST>(a, n0, n1, g);
     if ((f0 | f1) & F_EQ) eq_lanes<0>(a, n0, n1, f0, f1, g);
-    cell2_local_store_f32(a, n0, n1, f0, f1, g);
+    cell2_local_store_f32<FAST>(a, n0, n1, f0, f1, g);
 }
 
 // The neighbour step's per-cell scatter of a collided FP32 pair (l0 / l1: the lane takes this path;
-// a population heading into a solid goes to the cell's own reversed slot).  Every link is scattered
-// downstream; a link into a solid neighbour also goes to the own reversed slot.  Its downstream
-// store lands in the solid's slot that this same cell gathered its bounce-back from earlier in the
-// step, which nothing else reads before the next local step rewrites it.
+// a population heading into a solid goes to the cell's own reversed slot).  PLAIN: every link is
+// scattered downstream and a link into a solid neighbour also goes to the own reversed slot (its
+// downstream store lands in the solid's slot that this same cell gathered its bounce-back from
+// earlier in the step, which nothing else reads before the next local step rewrites it); else a
+// cell with solid neighbours selects one target per link.
+template <bool PLAIN = true>
 LBM_HD void cell2_neighbor_store_f32(const StepArgs &a, int n0, int n1, bool l0, bool l1, uint8_t f0, uint8_t f1,
                                      const float2 (&g)[Q]) {
     float *const *P = (float *const *)a.plane;
@@ -837,13 +854,27 @@ LBM_HD void cell2_neighbor_store_f32(const StepArgs &a, int n0, int n1, bool l0,
         if (!(c ? l1 : l0)) continue;
         const int n = c ? n1 : n0;
         const uint8_t fl = c ? f1 : f0;
+        if (PLAIN) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) P[i][n + a.off[i]] = c ? g[i].y : g[i].x;
-        if (fl & F_REDIR) {
-            const unsigned nb = a.info[n] >> 8;
+            for (int i = 0; i < Q; ++i) P[i][n + a.off[i]] = c ? g[i].y : g[i].x;
+            if (fl & F_REDIR) {
+                const unsigned nb = a.info[n] >> 8;
 #pragma unroll
-            for (int i = 0; i < Q; ++i)
-                if ((nb >> i) & 1u) P[opp(i)][n] = c ? g[i].y : g[i].x;
+                for (int i = 0; i < Q; ++i)
+                    if ((nb >> i) & 1u) P[opp(i)][n] = c ? g[i].y : g[i].x;
+            }
+            continue;
+        }
+        const unsigned nb = (fl & F_REDIR) ? a.info[n] >> 8 : 0u;
+        if (nb) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const bool bb = (nb >> i) & 1u;
+                (bb ? P[opp(i)] : P[i])[bb ? n : n + a.off[i]] = c ? g[i].y : g[i].x;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) P[i][n + a.off[i]] = c ? g[i].y : g[i].x;
         }
     }
 }
@@ -861,7 +892,7 @@ LBM_HD void cell2_neighbor_interior_dual_f32(const StepArgs &a, int n0, int n1, 
     const bool l0 = !(f0 & (F_SOLID | F_FACE)), l1 = !(f1 & (F_SOLID | F_FACE));
     if (!l0 && !l1) return;
     collide2_f32<FORCE, FAST>(a, n0, n1, g);
-    cell2_neighbor_store_f32(a, n0, n1, l0, l1, f0, f1, g);
+    cell2_neighbor_store_f32<FAST>(a, n0, n1, l0, l1, f0, f1, g);
 }
 
 // ---------------------------------------------------------------- ground and top layers in the lattice blocks
