@@ -347,6 +347,11 @@ LBM_HD void cell_face_table(const StepArgs &a, int t, uint32_t *__restrict__ tab
         int cnt = 0;
         if (!(fl & F_SOLID))
             scatter_targets(a.g, a.flags, x, y, z, j, fluid, [&](int kind, long long idx) {
+                // an equilibrium cell's stores into equilibrium cells are dropped: such a cell
+                // ignores what it receives (its next local step writes its equilibrium over it, and
+                // every read-back of it computes that equilibrium), and the equilibrium cell's own
+                // read-back does not look for its populations either
+                if (!fluid && kind == 0 && (a.flags[idx % a.g.N] & F_EQ)) return;
                 if (cnt < 2) v[cnt] = code(kind, idx);
                 ++cnt;
             });
